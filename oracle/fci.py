@@ -1,0 +1,160 @@
+"""Oracle CASCI: Slater-Condon Hamiltonian (C core) plus a library eigensolver.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and the CPU-baseline
+leg of bench.py use this module; the CUDA product path never imports it.
+
+The lowest eigenvalue of the determinant-basis Hamiltonian of a complete
+active space is the CASCI energy that every MBE-FCI term is built from (the
+"energy of a CASCI calculation" that defines epsilon in Eq. 1).  Determinant
+order and signs follow the convention stated in fci.c: alpha strings and beta
+strings in ascending bit-pattern order, index = I_a * N_b + I_b, creators in
+ascending spin-orbital order with all alpha orbitals before all beta ones.
+
+The eigensolver is a library routine: LAPACK (scipy.linalg.eigh) on the dense
+matrix for small spaces, ARPACK (scipy.sparse.linalg.eigsh) on the sparse
+matrix, or on an on-the-fly H*c operator, for larger ones.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import functools
+
+import numpy as np
+
+from . import build as _build
+
+DENSE_MAX = 1500
+SPARSE_MAX_ENTRIES = 30_000_000
+
+
+@functools.lru_cache(maxsize=1)
+def lib():
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    P = ctypes.c_void_p
+    L.oracle_binom.restype = i64
+    L.oracle_binom.argtypes = [i32, i32]
+    L.oracle_strings.restype = i64
+    L.oracle_strings.argtypes = [i32, i32, P]
+    L.oracle_hij.restype = dbl
+    L.oracle_hij.argtypes = [i32, P, P, ctypes.c_uint64, ctypes.c_uint64]
+    L.oracle_dets.restype = i32
+    L.oracle_dets.argtypes = [i32, i32, i32, P]
+    L.oracle_hdiag.restype = i32
+    L.oracle_hdiag.argtypes = [i32, i32, i32, P, P, P]
+    L.oracle_h_coo.restype = i64
+    L.oracle_h_coo.argtypes = [i32, i32, i32, P, P, i64, P, P, P]
+    L.oracle_sigma.restype = i32
+    L.oracle_sigma.argtypes = [i32, i32, i32, P, P, P, P]
+    return L
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype=np.float64):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def binom(n: int, k: int) -> int:
+    return int(lib().oracle_binom(n, k))
+
+
+def strings(n: int, k: int) -> np.ndarray:
+    """All k-electron strings over n orbitals as bit patterns, ascending."""
+    cnt = binom(n, k)
+    out = np.zeros(max(cnt, 1), dtype=np.uint64)
+    got = lib().oracle_strings(n, k, _ptr(out))
+    assert got == cnt
+    return out[:cnt]
+
+
+def dets(n: int, na: int, nb: int) -> np.ndarray:
+    """2n-bit determinant words in index order (alpha low bits, beta high bits)."""
+    N = binom(n, na) * binom(n, nb)
+    out = np.zeros(max(N, 1), dtype=np.uint64)
+    assert lib().oracle_dets(n, na, nb, _ptr(out)) == 0
+    return out[:N]
+
+
+def hij(h: np.ndarray, eri: np.ndarray, I: int, J: int) -> float:
+    h, eri = _c(h), _c(eri)
+    return float(lib().oracle_hij(h.shape[0], _ptr(h), _ptr(eri), int(I), int(J)))
+
+
+def hdiag(h: np.ndarray, eri: np.ndarray, na: int, nb: int) -> np.ndarray:
+    h, eri = _c(h), _c(eri)
+    n = h.shape[0]
+    N = binom(n, na) * binom(n, nb)
+    out = np.zeros(max(N, 1))
+    assert lib().oracle_hdiag(n, na, nb, _ptr(h), _ptr(eri), _ptr(out)) == 0
+    return out[:N]
+
+
+def h_coo(h: np.ndarray, eri: np.ndarray, na: int, nb: int):
+    """(rows, cols, vals) of the sparse Hamiltonian of the (na, nb) sector."""
+    h, eri = _c(h), _c(eri)
+    n = h.shape[0]
+    L = lib()
+    need = L.oracle_h_coo(n, na, nb, _ptr(h), _ptr(eri), 0, None, None, None)
+    cnt = -need if need < 0 else need
+    rows = np.zeros(max(cnt, 1), dtype=np.int64)
+    cols = np.zeros(max(cnt, 1), dtype=np.int64)
+    vals = np.zeros(max(cnt, 1))
+    got = L.oracle_h_coo(n, na, nb, _ptr(h), _ptr(eri), cnt, _ptr(rows), _ptr(cols), _ptr(vals))
+    assert got == cnt
+    return rows[:cnt], cols[:cnt], vals[:cnt]
+
+
+def h_dense(h: np.ndarray, eri: np.ndarray, na: int, nb: int) -> np.ndarray:
+    n = h.shape[0]
+    N = binom(n, na) * binom(n, nb)
+    rows, cols, vals = h_coo(h, eri, na, nb)
+    H = np.zeros((N, N))
+    np.add.at(H, (rows, cols), vals)
+    return H
+
+
+def sigma(h: np.ndarray, eri: np.ndarray, na: int, nb: int, c: np.ndarray) -> np.ndarray:
+    """sigma = H c for the (na, nb) sector, computed one connection at a time."""
+    h, eri, c = _c(h), _c(eri), _c(c)
+    n = h.shape[0]
+    N = binom(n, na) * binom(n, nb)
+    assert c.shape == (N,)
+    out = np.zeros(max(N, 1))
+    assert lib().oracle_sigma(n, na, nb, _ptr(h), _ptr(eri), _ptr(c), _ptr(out)) == 0
+    return out[:N]
+
+
+def lowest_eigenpair(h: np.ndarray, eri: np.ndarray, na: int, nb: int, tol: float = 1e-13,
+                     want_vector: bool = False):
+    """Lowest eigenvalue (and optionally its eigenvector) of the CAS Hamiltonian."""
+    import scipy.linalg
+    import scipy.sparse
+    import scipy.sparse.linalg
+
+    n = h.shape[0]
+    N = binom(n, na) * binom(n, nb)
+    if N == 0:
+        raise ValueError("empty determinant space")
+    if N <= DENSE_MAX:
+        H = h_dense(h, eri, na, nb)
+        w, v = scipy.linalg.eigh(H, subset_by_index=[0, 0])
+        return (float(w[0]), v[:, 0]) if want_vector else float(w[0])
+    conn = 1 + 2 * n * n + 4 * n ** 4
+    v0 = np.cos(np.arange(N) * 0.7311) + 0.1  # deterministic start vector
+    if N * conn <= SPARSE_MAX_ENTRIES:
+        rows, cols, vals = h_coo(h, eri, na, nb)
+        A = scipy.sparse.csr_matrix((vals, (rows, cols)), shape=(N, N))
+    else:
+        A = scipy.sparse.linalg.LinearOperator((N, N), matvec=lambda x: sigma(h, eri, na, nb, x),
+                                               dtype=np.float64)
+    w, v = scipy.sparse.linalg.eigsh(A, k=1, which="SA", tol=tol, v0=v0, ncv=min(N, 40))
+    return (float(w[0]), v[:, 0]) if want_vector else float(w[0])
+
+
+def lowest_eigenvalue(h, eri, na, nb, tol: float = 1e-13) -> float:
+    return lowest_eigenpair(h, eri, na, nb, tol=tol)
