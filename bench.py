@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark of the MBE-FCI tuple-CASCI hot path on GB300.
+
+One step = one pass of the whole hot path over the L=22 Hubbard-ring workload
+(t=1, U=4, half filling, momentum-basis orbitals, empty reference space,
+orders 1-6, tuples without an occupied or a virtual orbital skipped: 107,085
+tuple CASCIs of 2-6 orbitals and up to 400 determinants): device tuple
+enumeration, batched tuple CASCI, the increment recursion (Eq. 2) and the order
+sums and total (Eq. 1), all through the C ABI.
+
+Reported: tuple CASCI solves/s in mixed precision (the value) and in float64
+(side by side), the largest |mixed - float64| tuple-energy difference, the
+roofline of the dominant solver kernel, an end-to-end number through the
+public API with host inputs, and the oracle timed on a bounded sample on the
+host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "tuple CASCI solves/s at ≤1e-8 Eh, mixed vs FP64; sigma % of roofline"
+UNIT = "tuple CASCI solves/s"
+WORKLOAD = "hubbard22"
+WORKLOAD_DESC = ("Hubbard ring L=22 t=1 U=4 half filling, momentum-basis orbitals, empty reference, "
+                 "MBE orders 1-6 with the occupied/virtual skip rule (107,085 tuple CASCIs, "
+                 "2-6 orbitals, <=400 determinants)")
+L2_FLUSH_BYTES = 256 << 20
+
+# ALU peaks derived from unit counts and the maximum SM clock (2070 MHz, 152 SMs):
+#   float32: 128 FMA lanes/SM -> 152 * 128 * 2 flop * 2.07e9 = 80.5 TFLOP/s
+#   float64: the nominal GB300 rate, 1.25 TFLOP/s (about 2 FMA/clk/SM)
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+PEAK_FP64_TFLOPS = 1.25
+
+
+def sigma_flops_per_det(n: int, k: int) -> int:
+    """Algorithmic flops of one sigma element (direct string-driven form):
+    same-spin 2 * Ns FMAs, opposite-spin R^2 FMAs, 2 flops per FMA."""
+    ns = math.comb(n, k)
+    r = k * (n - k + 1)
+    return 2 * (2 * ns + r * r)
+
+
+DAVIDSON_FLOPS_PER_DET = 72  # residual, preconditioner, 2-pass orthogonalisation, 3x3 projections, update
+
+
+def solver_bucket(n: int, k: int):
+    """(solver, dpl) the library uses for a class: warp solver for <= 416 determinants."""
+    N = math.comb(n, k) ** 2
+    if n <= 8 and N <= 416:
+        for d in (1, 2, 4, 8, 13):
+            if d * 32 >= N:
+                return 0, d
+    return 1, 0
+
+
+# ----------------------------------------------------------------------------- utilities
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("casci.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1910_03527_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key: str):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "counters.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    e = rec.get(kernel_key)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------- oracle leg
+
+def oracle_sample(seconds: float, seed: int = 1910):
+    """Oracle tuple CASCIs on a seeded sample of the workload, stratified by order
+    in proportion to the tuple counts, for about `seconds` of single-core work."""
+    import numpy as np
+    from oracle import mbe as omb
+    from workloads import workload
+
+    w = workload(WORKLOAD)
+    e_phi = omb.phi_energy(w.h1, w.eri, w.occ)
+    lists = {n: omb.tuples(w.exp, w.ref, w.occ, n, w.skip) for n in w.orders}
+    total = sum(len(v) for v in lists.values())
+    rng = np.random.default_rng(seed)
+    # interleave orders in proportion to their counts
+    seq = []
+    for n in w.orders:
+        if lists[n]:
+            idx = rng.permutation(len(lists[n]))
+            seq += [(len(lists[n]) / total, i / len(lists[n]), n, lists[n][j]) for i, j in enumerate(idx)]
+    seq.sort(key=lambda x: x[1])
+    t0 = time.perf_counter()
+    done = 0
+    per_order = {}
+    for _, _, n, tup in seq:
+        omb.tuple_energy(w.h1, w.eri, w.occ, w.ref, tup, e_phi, 0.0)
+        done += 1
+        per_order[n] = per_order.get(n, 0) + 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"tuples": done, "seconds": dt, "per_order": per_order}
+
+
+def run_oracle_subprocess(seconds: float):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(seconds)],
+                         capture_output=True, text=True, env=env, cwd=ROOT, timeout=seconds * 4 + 120)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(res):
+    return {"value": res["tuples"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{res['tuples']} tuples of the same workload, seeded and stratified by order "
+                       f"({res['per_order']}), {res['seconds']:.1f} s, one thread")}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1910_03527_gb300 as eng
+    from workloads import workload
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    eng.build()
+    dev = torch.device("cuda", local)
+    ctx = eng.Context(local)
+    w = workload(WORKLOAD)
+    occ_host = w.occ.tolist()
+    h1 = torch.tensor(w.h1, device=dev)
+    eri = torch.tensor(w.eri, device=dev)
+    occ = torch.tensor(w.occ, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    mixed, fp64 = eng.Opts(precision="mixed"), eng.Opts(precision="fp64")
+
+    def step(opts):
+        return eng.run_mbe(ctx, h1, eri, occ, w.ref, w.exp, w.orders, w.skip, opts, occ_host=occ_host)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(mixed)
+        step(fp64)
+    torch.cuda.synchronize()
+
+    def timed(opts, sampler=None):
+        barrier()
+        torch.cuda.synchronize()
+        ctx.take_timings()
+        ctx.set_timing(True)
+        l0 = ctx.launches()
+        if sampler:
+            sampler.start()
+        evs, out = [], None
+        for _ in range(args.steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            out = step(opts)
+            e.record()
+            evs.append((s, e))
+        torch.cuda.synchronize()
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        launches = ctx.launches() - l0
+        recs = ctx.take_timings()
+        ctx.set_timing(False)
+        ms = [s.elapsed_time(e) for s, e in evs]
+        return ms, out, recs, launches, clocks
+
+    ms_mix, out_mix, recs_mix, launches, clocks = timed(mixed, ClockSampler(local))
+    ms_64, out_64, recs_64, _, _ = timed(fp64)
+
+    tot_mix = torch.tensor([sum(ms_mix)], dtype=torch.float64, device=dev)
+    tot_64 = torch.tensor([sum(ms_64)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(tot_mix, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot_64, op=dist.ReduceOp.MAX)
+    n_tuples = sum(int(t.shape[0]) for t in out_mix["tuples"])
+    ms_step_mix = tot_mix.item() / args.steps
+    ms_step_64 = tot_64.item() / args.steps
+    value_mix = ws * n_tuples / (ms_step_mix / 1e3)
+    value_64 = ws * n_tuples / (ms_step_64 / 1e3)
+
+    # accuracy of the mixed form against float64 on the same tuples
+    diff = max(float((a - b).abs().max().item()) for a, b in zip(out_mix["eps"], out_64["eps"]))
+    bad = sum(int((s != 0).sum().item()) for s in out_mix["status"] + out_64["status"])
+
+    # ---- roofline of the dominant solver kernel (per launch, CUDA events inside the library)
+    occ_np = np.asarray(w.occ)
+    per_bucket = {}
+    for (order, solver, dpl, ms) in recs_mix:
+        per_bucket.setdefault((order, solver, dpl), []).append(ms)
+    key = max(per_bucket, key=lambda k: sum(per_bucket[k]))
+    order, solver, dpl = key
+    i = w.orders.index(order)
+    tup = out_mix["tuples"][i].cpu().numpy()
+    iters = out_mix["iters"][i].cpu().numpy()
+    kk = occ_np[tup].sum(axis=1)
+    n = len(w.ref) + order
+    f64 = f32 = 0.0
+    for k in np.unique(kk):
+        if solver_bucket(n, int(k)) != (solver, dpl):
+            continue
+        sel = kk == k
+        per_it = sigma_flops_per_det(n, int(k)) + DAVIDSON_FLOPS_PER_DET
+        ndet = math.comb(n, int(k)) ** 2
+        f64 += float(((iters[sel] >> 16) & 0xffff).sum()) * per_it * ndet
+        f32 += float((iters[sel] & 0xffff).sum()) * per_it * ndet
+    launch_ms = statistics.mean(per_bucket[key])
+    t_s = launch_ms / 1e3
+    achieved = (f64 + f32 * PEAK_FP64_TFLOPS / PEAK_FP32_TFLOPS) / t_s / 1e12
+    kname = f"k_casci_warp<{dpl}>" if solver == 0 else "k_casci_block"
+    roofline = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS,
+                "unit": "TFLOP/s (float64-equivalent: float32 flops weighted by the "
+                        "float64:float32 peak ratio; peaks derived from unit counts at 2070 MHz)",
+                "frac": achieved / PEAK_FP64_TFLOPS,
+                "traffic": recorded_traffic(f"{kname}:order{order}"),
+                "kernel": kname, "launch": f"order {order} solver launch",
+                "ms_per_launch": launch_ms, "fp64_flop_per_launch": f64, "fp32_flop_per_launch": f32,
+                "fp64_tflops": f64 / t_s / 1e12, "fp32_tflops": f32 / t_s / 1e12,
+                "share_of_step": sum(per_bucket[key]) / sum(ms_mix)}
+
+    # ---- end to end through the public API with host inputs
+    h1_h = torch.tensor(w.h1).pin_memory()
+    eri_h = torch.tensor(w.eri).pin_memory()
+    occ_h = torch.tensor(w.occ).pin_memory()
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h1_d = h1_h.to(dev, non_blocking=True)
+        eri_d = eri_h.to(dev, non_blocking=True)
+        occ_d = occ_h.to(dev, non_blocking=True)
+        o = eng.run_mbe(ctx, h1_d, eri_d, occ_d, w.ref, w.exp, w.orders, w.skip, mixed, occ_host=occ_host)
+        e_order = o["e_order"].cpu()
+        e_total = o["e_total"].cpu()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = max(statistics.mean(e2e_times), 1e-12)
+    e2e = {"value": ws * n_tuples / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(h1_h.numel() * 8 + eri_h.numel() * 8 + occ_h.numel()),
+           "d2h_bytes_per_step": int((e_order.numel() + e_total.numel()) * 8),
+           "ms_per_step": e2e_s * 1e3, "clock": "host wall clock, synchronised"}
+
+    result = {
+        "metric": METRIC, "value": value_mix, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step_mix, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "tuples_per_step": n_tuples, "orders": "1-6",
+                   "precision": "mixed (float32 Davidson to residual 1e-4, then >= 2 float64 iterations "
+                                "to residual 1e-6)",
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": f"{ws} independent replica(s), no collective"},
+        "fp64": {"value": value_64, "unit": UNIT, "ms_per_step": ms_step_64, "dtype": "f64"},
+        "accuracy": {"max_abs_eps_mixed_minus_fp64_Eh": diff, "non_ok_status": bad,
+                     "e_total_mixed": float(out_mix["e_total"].item()),
+                     "e_total_fp64": float(out_64["e_total"].item())},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline_entry(run_oracle_subprocess(args.cpu_seconds))
+    if rank == 0:
+        print(json.dumps(result))
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The oracle as it stands, on the host cores: each step is a bounded sample
+    of the same workload, timed on the wall clock."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        run_oracle_subprocess(args.ref_step_seconds / 4)
+    done = secs = 0.0
+    per = []
+    for _ in range(args.steps):
+        r = run_oracle_subprocess(args.ref_step_seconds)
+        done += r["tuples"]
+        secs += r["seconds"]
+        per.append(r)
+    value = done / secs
+    res = {"tuples": int(done), "seconds": secs, "per_order": per[-1]["per_order"]}
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD_DESC, "orders": "1-6",
+                      "sample": f"each step: about {args.ref_step_seconds:.0f} s of oracle tuple CASCIs "
+                                "from a seeded, order-stratified sample"},
+           "cpu_baseline": cpu_baseline_entry(res),
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=8.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.oracle_sample is not None:
+        print(json.dumps(oracle_sample(args.oracle_sample)))
+        return
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,263 @@
+/*
+ * mbe.h -- C ABI of the GB300 (sm_103a) engine for the MBE-FCI tuple-CASCI
+ * hot path (generalized many-body expanded full configuration interaction).
+ *
+ * The method: the orbitals are split into a reference space R and an
+ * expansion space X (Eq. 1).  Every tuple Omega of n expansion orbitals
+ * defines a complete active space A = R u Omega whose CASCI energy gives the
+ * tuple energy eps(Omega); the increments of Eq. 2,
+ *     Delta eps(Omega) = eps(Omega) - sum over proper sub-tuples S of Delta eps(S),
+ * summed order by order give E = E_ref + E^(1) + E^(2) + ... (Eq. 1, and Eq. 3
+ * for an empty, "vacuum", reference space).
+ *
+ * Conventions shared by every call:
+ *  - Integrals are real, float64, row-major: h1[p*norb+q] = h_pq and
+ *    eri[((p*norb+q)*norb+r)*norb+s] = (pq|rs) in chemists' notation, with the
+ *    8-fold permutational symmetry of real orbitals.
+ *  - occ[p] = 1 marks an orbital doubly occupied in the closed-shell reference
+ *    determinant Phi, 0 a virtual one.
+ *  - Orbital indices are 0-based global indices.  Tuples are rows of `order`
+ *    int32 indices, each row strictly ascending; tuple lists are in
+ *    lexicographic order (the order mbe_tuples produces).
+ *  - "device" pointers are CUDA global memory of the context's device; "host"
+ *    pointers are ordinary host memory.  The caller allocates and owns every
+ *    input and output buffer; the library owns only its context's workspace
+ *    and string-table cache.
+ *  - Calls are asynchronous on the context's stream unless stated otherwise.
+ *  - Every call returns MBE_OK (0) or a negative MBE_E* code; mbe_last_error()
+ *    then describes the failure.  No call aborts, exits or traps on the device.
+ */
+#ifndef MBE_H
+#define MBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ errors */
+#define MBE_OK 0
+#define MBE_EINVAL (-1)       /* an argument is out of range or inconsistent   */
+#define MBE_ENOMEM (-2)       /* device or host allocation failed              */
+#define MBE_ECUDA (-3)        /* a CUDA runtime call failed                    */
+#define MBE_EUNSUPPORTED (-4) /* sizes beyond the compiled limits (see below)  */
+
+/* Compiled limits. */
+#define MBE_MAX_NORB 64       /* orbitals in the full space                    */
+#define MBE_MAX_CAS 12        /* orbitals in one tuple active space |R u Omega| */
+#define MBE_MAX_ORDER 16      /* tuple order n                                 */
+#define MBE_MAX_STRING_ORB 16 /* orbitals of one string table (mbe_string_table) */
+
+/* Per-tuple status codes written by casci_batch. */
+#define MBE_STATUS_OK 0        /* converged: residual 2-norm <= tol              */
+#define MBE_STATUS_MAXITER 1   /* iteration cap reached; eps holds the last Ritz value */
+#define MBE_STATUS_NONFINITE 2 /* a NaN or Inf appeared; eps is NaN              */
+#define MBE_STATUS_BADINPUT 3  /* malformed tuple (index range, order, overlap with R) */
+
+/* Tuple-enumeration flags. */
+#define MBE_SKIP_NO_OCC_OR_VIRT 1 /* drop a tuple whose active space R u Omega has no
+                                     occupied or no virtual orbital (such tuples have
+                                     vanishing increments for an empty reference space,
+                                     the statement after Eq. 3) */
+
+/* Precision modes of casci_batch. */
+#define MBE_PREC_FP64 0  /* every sigma and every Davidson step in float64             */
+#define MBE_PREC_MIXED 1 /* float32 sigma and Davidson until the residual reaches
+                            tol_switch, then at least fp64_final_iters float64
+                            Davidson iterations; the residual norm, Rayleigh quotient
+                            and subspace eigenproblem that decide convergence and give
+                            eps are float64                                          */
+
+typedef struct mbe_ctx mbe_ctx;
+
+typedef struct mbe_opts {
+    int precision;        /* MBE_PREC_FP64 or MBE_PREC_MIXED                       */
+    double tol;           /* converged when ||H x - lambda x||_2 <= tol (x unit norm) */
+    double tol_switch;    /* mixed mode: float32 phase ends at this residual         */
+    int max_iter;         /* cap on Davidson iterations per phase                    */
+    int fp64_final_iters; /* mixed mode: minimum float64 iterations                  */
+} mbe_opts;
+
+/* Fills *opts with the defaults: FP64, tol 1e-6, tol_switch 1e-4, max_iter 200,
+   fp64_final_iters 2.  Host only, synchronous. */
+void mbe_default_opts(mbe_opts *opts);
+
+/* ------------------------------------------------------------------ context */
+
+/* Creates a context on CUDA device `device`, issuing work on `cuda_stream`
+   (a cudaStream_t; NULL = the legacy default stream).  The context owns a
+   growable device workspace and a cache of string tables.  Synchronous.
+   Errors: MBE_EINVAL (ctx NULL or bad device), MBE_ECUDA, MBE_ENOMEM. */
+int mbe_ctx_create(mbe_ctx **ctx, int device, void *cuda_stream);
+
+/* Changes the stream later calls issue work on.  Host only. */
+int mbe_ctx_set_stream(mbe_ctx *ctx, void *cuda_stream);
+
+/* Waits for all work of the context, frees its workspace and the context. */
+void mbe_ctx_destroy(mbe_ctx *ctx);
+
+/* Text of the last error raised by a call on this thread (never NULL). */
+const char *mbe_last_error(void);
+
+/* Synchronises the context's stream and reports any pending CUDA error. */
+int mbe_ctx_sync(mbe_ctx *ctx);
+
+/* Number of kernels this context has launched since it was created.  Host only. */
+int mbe_ctx_launches(const mbe_ctx *ctx, int64_t *count);
+
+/* Per-launch timing of the tuple-CASCI solver kernels, for measurement.  While
+   enabled, casci_batch brackets every solver launch with a pair of CUDA events
+   on the context's stream.  mbe_ctx_timings synchronises the stream, copies up
+   to `max` records into `out` (host), sets *count to the number of records and
+   clears them.  solver: 0 = one tuple per warp (dpl = determinants per lane),
+   1 = one tuple per thread block.  Not for use during stream capture. */
+typedef struct mbe_timing {
+    int order;  /* tuple order of the casci_batch call   */
+    int solver; /* 0 warp solver, 1 block solver          */
+    int dpl;    /* determinants per lane (warp solver)    */
+    float ms;   /* elapsed time of the launch             */
+} mbe_timing;
+int mbe_ctx_set_timing(mbe_ctx *ctx, int enable);
+int mbe_ctx_timings(mbe_ctx *ctx, int max, mbe_timing *out, int *count);
+
+/* ------------------------------------------------------------------ a1: tuples */
+
+/*
+ * Tuple enumeration (Eq. 2's order-n tuples; skip rule after Eq. 3).
+ * All order-`order` subsets of the expansion space, listed in lexicographic
+ * order of the sorted expansion orbitals, optionally without the tuples that
+ * MBE_SKIP_NO_OCC_OR_VIRT drops.
+ *   exp_orbs [n_exp]  host, distinct orbital indices (any order; sorted inside)
+ *   ref_orbs [n_ref]  host, the reference space (only used by the skip rule)
+ *   occ      [norb]   host, reference occupations
+ *   n_tuples          host out: number of tuples
+ *   tuples   [n_tuples*order] device out, or NULL to query the count only
+ *                     (the count query is synchronous and launches nothing).
+ * The enumeration itself runs on the device: rank -> lexicographic unranking ->
+ * filter -> order-preserving compaction.
+ * Errors: MBE_EINVAL (bad indices, order < 1 or > n_exp, order > MBE_MAX_ORDER),
+ * MBE_ECUDA.
+ */
+int mbe_tuples(mbe_ctx *ctx, int norb, const uint8_t *occ, int n_exp, const int32_t *exp_orbs,
+               int n_ref, const int32_t *ref_orbs, int order, int flags, int64_t *n_tuples,
+               int32_t *tuples);
+
+/* ------------------------------------------------------------------ a3: strings */
+
+/*
+ * String table of one (n_orb, n_el) class, built on the device.
+ *   strings [C(n_orb, n_el)]            device out (uint32 bit patterns), ascending;
+ *                                       string rank = sum_i C(c_i, i) over its set bits
+ *                                       c_1 < c_2 < ... (combinatorial number system)
+ *   table   [C(n_orb,n_el) * n_el*(n_orb-n_el+1)]  device out, or NULL.
+ * Row I lists every non-zero single replacement E_pq |I> = sign |J> (q occupied in
+ * I, p empty in I or p == q), ordered by q ascending then p ascending, packed as
+ *   entry = (J << 9) | (pair(p,q) << 1) | (sign < 0),
+ * pair(p,q) = max(p,q)*(max(p,q)+1)/2 + min(p,q);  sign = (-1)^(number of occupied
+ * orbitals of I strictly between p and q).  These replacement lists carry the
+ * CASCI sigma (the CASCI solver is the one the paper names; the layout is ours).
+ * Errors: MBE_EINVAL, MBE_EUNSUPPORTED (n_orb > MBE_MAX_STRING_ORB), MBE_ECUDA.
+ */
+int mbe_string_table(mbe_ctx *ctx, int n_orb, int n_el, uint32_t *strings, int32_t *table);
+
+/* ------------------------------------------------------------------ a2-a7: CASCI */
+
+/*
+ * Reference-determinant energy E_Phi = sum_{i in O} 2 h_ii + sum_{i,j in O}
+ * [2 (ii|jj) - (ij|ji)], O = {p : occ[p] = 1}.  h1, eri, occ device; e_phi device
+ * out (one double).
+ */
+int mbe_phi_energy(mbe_ctx *ctx, int norb, const double *h1, const double *eri,
+                   const uint8_t *occ, double *e_phi);
+
+/*
+ * Batched tuple CASCI (eps in Eq. 1 and Eq. 2).  For every tuple t:
+ *   A = R u tuple_t (sorted), n_alpha = n_beta = |O n A|; the orbitals of O outside
+ *   A are a frozen core (their mean field enters through the core Fock matrix
+ *   F = h + sum_{i in O}(2 J_i - K_i), computed on the device), the other
+ *   orbitals are deleted; lambda = lowest eigenvalue of the active-space
+ *   Hamiltonian in the (n_alpha, n_beta) determinant sector, found by a batched
+ *   Davidson solver; and
+ *     eps_out[t] = lambda - <Phi_A|H_A|Phi_A> - e_ref_corr,
+ *   which equals E_CAS(A) - E_Phi - e_ref_corr.
+ *   h1 [norb^2], eri [norb^4], occ [norb]   device
+ *   ref_orbs [n_ref]                         host, sorted, disjoint from tuples
+ *   e_ref_corr                               E_CAS(R) - E_Phi (0 for R empty)
+ *   tuples [n_tuples*order]                  device; order 0 is allowed with n_tuples = 1
+ *                                            and tuples = NULL: the CAS is R itself, and
+ *                                            with e_ref_corr = 0 the call returns
+ *                                            E_ref,corr = E_CAS(R) - E_Phi
+ *   opts                                     host; NULL = mbe_default_opts
+ *   eps_out [n_tuples]                       device out
+ *   status_out [n_tuples]                    device out, MBE_STATUS_*
+ *   iters_out [n_tuples]                     device out or NULL: sigma products used
+ *                                            (float64 ones in the high 16 bits,
+ *                                            float32 ones in the low 16 bits)
+ * |R| + order <= MBE_MAX_CAS.  Tuple problems of up to 416 determinants run one per
+ * warp with the Davidson vectors in registers; larger ones one per thread block
+ * with the vectors in the context's device workspace.
+ * Errors: MBE_EINVAL, MBE_EUNSUPPORTED, MBE_ENOMEM, MBE_ECUDA.  A malformed tuple is
+ * not an error of the call: its status is MBE_STATUS_BADINPUT and its eps NaN.
+ */
+int casci_batch(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
+                int n_ref, const int32_t *ref_orbs, double e_ref_corr, int order,
+                int64_t n_tuples, const int32_t *tuples, const mbe_opts *opts, double *eps_out,
+                int32_t *status_out, int32_t *iters_out);
+
+/*
+ * One sigma product sigma = H_A c for a single active space (the inner kernel of
+ * casci_batch, exposed for parity tests and sigma throughput measurement).
+ *   cas_orbs [n_cas] host, sorted; the active space A
+ *   c, sigma [C(n_cas,k)^2] device, float64, determinant index I_a*N_b + I_b with
+ *            strings in ascending bit-pattern order, k = |O n A|
+ *   diag     [C(n_cas,k)^2] device out or NULL: the diagonal H_II
+ * Errors: MBE_EINVAL, MBE_EUNSUPPORTED, MBE_ENOMEM, MBE_ECUDA.
+ */
+int casci_sigma(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
+                int n_cas, const int32_t *cas_orbs, const double *c, double *sigma,
+                double *diag);
+
+/* ------------------------------------------------------------------ a8-a9: Eqs. 2, 1 */
+
+/*
+ * Increment recursion, Eq. 2, for the tuples of one order:
+ *   inc_out[t] = eps[t] - sum over every proper, non-empty subset S of tuple t of
+ *                Delta eps(S),
+ * where Delta eps(S) is looked up (binary search) in the lower-order lists; a
+ * subset absent from its list (a skipped tuple) contributes 0.  The subsets are
+ * visited in a fixed order (bit mask 1 .. 2^order-2 over the tuple's positions),
+ * so the result is deterministic.
+ *   tuples [n_tuples*order], eps [n_tuples]              device
+ *   n_lower                                              number of lower orders given
+ *                                                        (must be order - 1)
+ *   n_lower_tuples [n_lower]                             host: list lengths, orders 1..n_lower
+ *   lower_tuples [n_lower], lower_incs [n_lower]         host arrays of device pointers;
+ *                                                        lower_tuples[m-1] holds order-m
+ *                                                        tuples in lexicographic order
+ *   inc_out [n_tuples]                                   device out
+ * Errors: MBE_EINVAL, MBE_ECUDA.
+ */
+int mbe_increments(mbe_ctx *ctx, int order, int64_t n_tuples, const int32_t *tuples,
+                   const double *eps, int n_lower, const int64_t *n_lower_tuples,
+                   const int32_t *const *lower_tuples, const double *const *lower_incs,
+                   double *inc_out);
+
+/*
+ * Order sums and total, Eq. 1 (Eq. 3 for an empty reference space):
+ *   e_order_out[m] = sum_t incs[m][t]          (fixed-shape tree reduction)
+ *   e_total_out[0] = e_phi + e_ref_corr + sum_m e_order_out[m]
+ *   n_tuples [n_orders], incs [n_orders]       host arrays (incs: device pointers)
+ *   e_phi                                      device pointer to one double, or NULL
+ *                                              for 0 (e.g. to sum correlation only)
+ *   e_order_out [n_orders], e_total_out [1]    device out
+ * Errors: MBE_EINVAL, MBE_ECUDA.
+ */
+int mbe_total(mbe_ctx *ctx, int n_orders, const int64_t *n_tuples, const double *const *incs,
+              const double *e_phi, double e_ref_corr, double *e_order_out, double *e_total_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBE_H */

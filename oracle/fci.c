@@ -300,3 +300,30 @@ int oracle_sigma(int n, int na, int nb, const double *h, const double *eri, cons
     space_free(&s);
     return 0;
 }
+
+/*
+ * Selected rows of sigma = H c: out[i] = sum_J <rows[i]|H|J> c_J, with J running
+ * over the determinants connected to rows[i].  For spaces too large for a full
+ * oracle sigma.
+ */
+int oracle_sigma_rows(int n, int na, int nb, const double *h, const double *eri, const double *c,
+                      int64_t nrows, const int64_t *rows, double *out)
+{
+    space_t s;
+    if (space_init(&s, n, na, nb)) return -1;
+    word *con = (word *)malloc(sizeof(word) * (size_t)max_connections(n));
+    for (int64_t r = 0; r < nrows; ++r) {
+        word I = det_word(&s, rows[r]);
+        int64_t nc = connections(n, I, con);
+        double acc = 0.0;
+        for (int64_t k = 0; k < nc; ++k) {
+            int64_t j = det_index(&s, con[k]);
+            if (j < 0) continue;
+            acc += oracle_hij(n, h, eri, I, con[k]) * c[j];
+        }
+        out[r] = acc;
+    }
+    free(con);
+    space_free(&s);
+    return 0;
+}

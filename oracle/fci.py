@@ -48,6 +48,8 @@ def lib():
     L.oracle_h_coo.argtypes = [i32, i32, i32, P, P, i64, P, P, P]
     L.oracle_sigma.restype = i32
     L.oracle_sigma.argtypes = [i32, i32, i32, P, P, P, P]
+    L.oracle_sigma_rows.restype = i32
+    L.oracle_sigma_rows.argtypes = [i32, i32, i32, P, P, P, i64, P, P]
     return L
 
 
@@ -127,6 +129,17 @@ def sigma(h: np.ndarray, eri: np.ndarray, na: int, nb: int, c: np.ndarray) -> np
     out = np.zeros(max(N, 1))
     assert lib().oracle_sigma(n, na, nb, _ptr(h), _ptr(eri), _ptr(c), _ptr(out)) == 0
     return out[:N]
+
+
+def sigma_rows(h: np.ndarray, eri: np.ndarray, na: int, nb: int, c: np.ndarray,
+               rows) -> np.ndarray:
+    """Selected rows of H c, each from the connections of that determinant."""
+    h, eri, c = _c(h), _c(eri), _c(c)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.zeros(max(len(rows), 1))
+    assert lib().oracle_sigma_rows(h.shape[0], na, nb, _ptr(h), _ptr(eri), _ptr(c), len(rows),
+                                   _ptr(rows), _ptr(out)) == 0
+    return out[: len(rows)]
 
 
 def lowest_eigenpair(h: np.ndarray, eri: np.ndarray, na: int, nb: int, tol: float = 1e-13,

@@ -1,0 +1,20 @@
+"""GB300 (sm_103a) engine for the MBE-FCI tuple-CASCI hot path.
+
+The compute lives in libmbe_gb300.so (CUDA kernels behind the C ABI of
+include/mbe.h).  This package is its thin ctypes binding: ``Context`` wraps an
+``mbe_ctx`` and exposes the ABI calls under the same names, and ``run_mbe``
+strings them into one pass of the hot path (tuples -> tuple CASCI ->
+increments -> totals).
+"""
+
+from .binding import (  # noqa: F401
+    EXPORTS,
+    Context,
+    MbeError,
+    Opts,
+    STATUS_NAMES,
+    lib,
+    library_path,
+    run_mbe,
+)
+from ._build import build  # noqa: F401

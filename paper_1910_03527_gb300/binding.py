@@ -1,0 +1,329 @@
+"""Python binding of the C ABI in include/mbe.h (argument marshalling only).
+
+Every computation runs in the CUDA kernels of libmbe_gb300.so.  This module
+only checks tensor placement, dtype and contiguity, passes raw pointers and
+sizes through ctypes, and allocates output tensors with PyTorch on the
+context's device.  There is no CPU fallback: without the library or a CUDA
+device every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import functools
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import _build
+
+MBE_OK = 0
+MBE_PREC_FP64 = 0
+MBE_PREC_MIXED = 1
+MBE_SKIP_NO_OCC_OR_VIRT = 1
+MBE_MAX_CAS = 12
+STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "NONFINITE", 3: "BADINPUT"}
+
+EXPORTS = ("mbe_default_opts", "mbe_ctx_create", "mbe_ctx_set_stream", "mbe_ctx_destroy",
+           "mbe_last_error", "mbe_ctx_sync", "mbe_ctx_launches", "mbe_ctx_set_timing",
+           "mbe_ctx_timings", "mbe_tuples", "mbe_string_table", "mbe_phi_energy",
+           "casci_batch", "casci_sigma", "mbe_increments", "mbe_total")
+
+
+class MbeOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double),
+                ("tol_switch", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("fp64_final_iters", ctypes.c_int)]
+
+
+class MbeTiming(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("solver", ctypes.c_int), ("dpl", ctypes.c_int),
+                ("ms", ctypes.c_float)]
+
+
+class MbeError(RuntimeError):
+    pass
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+@functools.lru_cache(maxsize=1)
+def lib() -> ctypes.CDLL:
+    """Load libmbe_gb300.so (it must have been built: __graft_entry__.build())."""
+    path = library_path()
+    if not os.path.exists(path):
+        raise MbeError(f"{path} is missing; build it first (python -c 'import __graft_entry__ as g; "
+                       "g.build()')")
+    L = ctypes.CDLL(path)
+    P, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    L.mbe_default_opts.restype = None
+    L.mbe_default_opts.argtypes = [ctypes.POINTER(MbeOpts)]
+    L.mbe_ctx_create.restype = i32
+    L.mbe_ctx_create.argtypes = [ctypes.POINTER(P), i32, P]
+    L.mbe_ctx_set_stream.restype = i32
+    L.mbe_ctx_set_stream.argtypes = [P, P]
+    L.mbe_ctx_destroy.restype = None
+    L.mbe_ctx_destroy.argtypes = [P]
+    L.mbe_last_error.restype = ctypes.c_char_p
+    L.mbe_last_error.argtypes = []
+    L.mbe_ctx_sync.restype = i32
+    L.mbe_ctx_sync.argtypes = [P]
+    L.mbe_ctx_launches.restype = i32
+    L.mbe_ctx_launches.argtypes = [P, ctypes.POINTER(i64)]
+    L.mbe_ctx_set_timing.restype = i32
+    L.mbe_ctx_set_timing.argtypes = [P, i32]
+    L.mbe_ctx_timings.restype = i32
+    L.mbe_ctx_timings.argtypes = [P, i32, ctypes.POINTER(MbeTiming), ctypes.POINTER(i32)]
+    L.mbe_tuples.restype = i32
+    L.mbe_tuples.argtypes = [P, i32, P, i32, P, i32, P, i32, i32, ctypes.POINTER(i64), P]
+    L.mbe_string_table.restype = i32
+    L.mbe_string_table.argtypes = [P, i32, i32, P, P]
+    L.mbe_phi_energy.restype = i32
+    L.mbe_phi_energy.argtypes = [P, i32, P, P, P, P]
+    L.casci_batch.restype = i32
+    L.casci_batch.argtypes = [P, i32, P, P, P, i32, P, dbl, i32, i64, P, ctypes.POINTER(MbeOpts),
+                              P, P, P]
+    L.casci_sigma.restype = i32
+    L.casci_sigma.argtypes = [P, i32, P, P, P, i32, P, P, P, P]
+    L.mbe_increments.restype = i32
+    L.mbe_increments.argtypes = [P, i32, i64, P, P, i32, P, P, P, P]
+    L.mbe_total.restype = i32
+    L.mbe_total.argtypes = [P, i32, P, P, P, dbl, P, P]
+    return L
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != MBE_OK:
+        msg = lib().mbe_last_error().decode(errors="replace")
+        raise MbeError(f"{what} failed ({rc}): {msg}")
+
+
+def _i32_host(values: Sequence[int]):
+    arr = (ctypes.c_int32 * max(len(values), 1))(*[int(v) for v in values])
+    return arr
+
+
+def _u8_host(values: Sequence[int]):
+    return (ctypes.c_uint8 * max(len(values), 1))(*[int(v) for v in values])
+
+
+@dataclass
+class Opts:
+    """Davidson options of casci_batch (see mbe_opts in include/mbe.h)."""
+
+    precision: str = "fp64"  # "fp64" or "mixed"
+    tol: float = 1e-6
+    tol_switch: float = 1e-4
+    max_iter: int = 200
+    fp64_final_iters: int = 2
+
+    def to_c(self) -> MbeOpts:
+        o = MbeOpts()
+        o.precision = {"fp64": MBE_PREC_FP64, "mixed": MBE_PREC_MIXED}[self.precision]
+        o.tol = self.tol
+        o.tol_switch = self.tol_switch
+        o.max_iter = self.max_iter
+        o.fp64_final_iters = self.fp64_final_iters
+        return o
+
+
+class Context:
+    """An mbe_ctx bound to one CUDA device; work is issued on `stream`."""
+
+    def __init__(self, device: int = 0, stream: Optional[torch.cuda.Stream] = None):
+        if not torch.cuda.is_available():
+            raise MbeError("no CUDA device: the MBE-FCI engine has no CPU path")
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        _check(lib().mbe_ctx_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream)),
+               "mbe_ctx_create")
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().mbe_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream: torch.cuda.Stream) -> None:
+        self.stream = stream
+        _check(lib().mbe_ctx_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)), "mbe_ctx_set_stream")
+
+    def sync(self) -> None:
+        _check(lib().mbe_ctx_sync(self._h), "mbe_ctx_sync")
+
+    def launches(self) -> int:
+        """Kernels launched by this context so far."""
+        n = ctypes.c_int64()
+        _check(lib().mbe_ctx_launches(self._h, ctypes.byref(n)), "mbe_ctx_launches")
+        return n.value
+
+    def set_timing(self, enable: bool) -> None:
+        _check(lib().mbe_ctx_set_timing(self._h, 1 if enable else 0), "mbe_ctx_set_timing")
+
+    def take_timings(self, max_records: int = 4096):
+        """[(order, solver, dpl, ms)] of the timed solver launches since the last read."""
+        buf = (MbeTiming * max_records)()
+        cnt = ctypes.c_int()
+        _check(lib().mbe_ctx_timings(self._h, max_records, buf, ctypes.byref(cnt)), "mbe_ctx_timings")
+        return [(buf[i].order, buf[i].solver, buf[i].dpl, buf[i].ms) for i in range(min(cnt.value,
+                                                                                       max_records))]
+
+    # ---------------------------------------------------------------- helpers
+    def _dev(self, t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != dtype:
+            raise MbeError(f"{name}: expected a {dtype} tensor on {self.device}")
+        if not t.is_contiguous():
+            raise MbeError(f"{name}: must be contiguous")
+        return t
+
+    @staticmethod
+    def _p(t: Optional[torch.Tensor]):
+        return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else None
+
+    def _empty(self, shape, dtype):
+        return torch.empty(shape, dtype=dtype, device=self.device)
+
+    # ---------------------------------------------------------------- ABI calls
+    def mbe_tuples(self, norb: int, occ: Sequence[int], exp: Sequence[int], ref: Sequence[int],
+                   order: int, skip: bool) -> torch.Tensor:
+        n = ctypes.c_int64()
+        flags = MBE_SKIP_NO_OCC_OR_VIRT if skip else 0
+        occ_h, exp_h, ref_h = _u8_host(occ), _i32_host(exp), _i32_host(ref)
+        _check(lib().mbe_tuples(self._h, norb, occ_h, len(exp), exp_h, len(ref), ref_h, order, flags,
+                                ctypes.byref(n), None), "mbe_tuples(count)")
+        out = self._empty((n.value, order), torch.int32)
+        if n.value > 0:
+            _check(lib().mbe_tuples(self._h, norb, occ_h, len(exp), exp_h, len(ref), ref_h, order,
+                                    flags, ctypes.byref(n), self._p(out)), "mbe_tuples")
+        return out
+
+    def mbe_string_table(self, n_orb: int, n_el: int):
+        import math
+        ns = math.comb(n_orb, n_el)
+        r = n_el * (n_orb - n_el + 1)
+        strings = self._empty((ns,), torch.int32)
+        table = self._empty((ns, r), torch.int32)
+        _check(lib().mbe_string_table(self._h, n_orb, n_el, self._p(strings), self._p(table)),
+               "mbe_string_table")
+        return strings, table
+
+    def mbe_phi_energy(self, h1, eri, occ) -> torch.Tensor:
+        norb = h1.shape[0]
+        out = self._empty((1,), torch.float64)
+        _check(lib().mbe_phi_energy(self._h, norb, self._p(self._dev(h1, torch.float64, "h1")),
+                                    self._p(self._dev(eri, torch.float64, "eri")),
+                                    self._p(self._dev(occ, torch.uint8, "occ")), self._p(out)),
+               "mbe_phi_energy")
+        return out
+
+    def casci_batch(self, h1, eri, occ, ref: Sequence[int], e_ref_corr: float, order: int,
+                    tuples: Optional[torch.Tensor], opts: Optional[Opts] = None, n_tuples=None,
+                    out=None):
+        norb = h1.shape[0]
+        if tuples is not None:
+            self._dev(tuples, torch.int32, "tuples")
+            n_t = tuples.shape[0] if n_tuples is None else n_tuples
+        else:
+            n_t = 1 if n_tuples is None else n_tuples
+        if out is None:
+            eps = self._empty((n_t,), torch.float64)
+            status = self._empty((n_t,), torch.int32)
+            iters = self._empty((n_t,), torch.int32)
+        else:
+            eps, status, iters = out
+        o = (opts or Opts()).to_c()
+        ref_h = _i32_host(ref)
+        _check(lib().casci_batch(self._h, norb, self._p(self._dev(h1, torch.float64, "h1")),
+                                 self._p(self._dev(eri, torch.float64, "eri")),
+                                 self._p(self._dev(occ, torch.uint8, "occ")), len(ref), ref_h,
+                                 float(e_ref_corr), order, n_t, self._p(tuples), ctypes.byref(o),
+                                 self._p(eps), self._p(status), self._p(iters)), "casci_batch")
+        return eps, status, iters
+
+    def casci_sigma(self, h1, eri, occ, cas: Sequence[int], c: torch.Tensor, want_diag: bool = True):
+        norb = h1.shape[0]
+        self._dev(c, torch.float64, "c")
+        sigma = torch.empty_like(c)
+        diag = torch.empty_like(c) if want_diag else None
+        cas_h = _i32_host(cas)
+        _check(lib().casci_sigma(self._h, norb, self._p(self._dev(h1, torch.float64, "h1")),
+                                 self._p(self._dev(eri, torch.float64, "eri")),
+                                 self._p(self._dev(occ, torch.uint8, "occ")), len(cas), cas_h,
+                                 self._p(c), self._p(sigma), self._p(diag)), "casci_sigma")
+        return sigma, diag
+
+    def mbe_increments(self, order: int, tuples: torch.Tensor, eps: torch.Tensor,
+                       lower_tuples: List[torch.Tensor], lower_incs: List[torch.Tensor],
+                       out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        n_t = tuples.shape[0]
+        inc = self._empty((n_t,), torch.float64) if out is None else out
+        nl = len(lower_tuples)
+        counts = (ctypes.c_int64 * max(nl, 1))(*[int(t.shape[0]) for t in lower_tuples])
+        tp = (ctypes.c_void_p * max(nl, 1))(*[self._p(t) for t in lower_tuples])
+        ip = (ctypes.c_void_p * max(nl, 1))(*[self._p(t) for t in lower_incs])
+        for t in lower_tuples:
+            self._dev(t, torch.int32, "lower tuples")
+        for t in lower_incs:
+            self._dev(t, torch.float64, "lower increments")
+        _check(lib().mbe_increments(self._h, order, n_t, self._p(self._dev(tuples, torch.int32, "tuples")),
+                                    self._p(self._dev(eps, torch.float64, "eps")), nl, counts, tp, ip,
+                                    self._p(inc)), "mbe_increments")
+        return inc
+
+    def mbe_total(self, incs: List[torch.Tensor], e_phi: Optional[torch.Tensor], e_ref_corr: float,
+                  out=None):
+        n = len(incs)
+        e_order = self._empty((max(n, 1),), torch.float64) if out is None else out[0]
+        e_total = self._empty((1,), torch.float64) if out is None else out[1]
+        counts = (ctypes.c_int64 * max(n, 1))(*[int(t.shape[0]) for t in incs])
+        ip = (ctypes.c_void_p * max(n, 1))(*[self._p(t) for t in incs])
+        _check(lib().mbe_total(self._h, n, counts, ip, self._p(e_phi), float(e_ref_corr),
+                               self._p(e_order), self._p(e_total)), "mbe_total")
+        return e_order[:n], e_total
+
+
+def run_mbe(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequence[int],
+            orders: Sequence[int], skip: bool, opts: Optional[Opts] = None,
+            occ_host: Optional[Sequence[int]] = None):
+    """One pass of the whole hot path through the C ABI: tuples, tuple CASCI,
+    increments (Eq. 2) and the order sums and total (Eq. 1), all on the device.
+
+    h1, eri, occ are device tensors.  Returns a dict of device tensors (per-order
+    tuples, eps, status, iters, increments; e_order, e_total, e_phi) and the
+    reference-space correlation energy used.
+    """
+    occ_h = [int(v) for v in (occ_host if occ_host is not None else occ.cpu().tolist())]
+    norb = h1.shape[0]
+    e_phi = ctx.mbe_phi_energy(h1, eri, occ)
+    e_ref = 0.0
+    if len(ref) > 0:
+        eps_r, st_r, _ = ctx.casci_batch(h1, eri, occ, ref, 0.0, 0, None, opts)
+        e_ref = float(eps_r.item())
+    out = dict(tuples=[], eps=[], status=[], iters=[], inc=[], e_phi=e_phi, e_ref_corr=e_ref)
+    for n in orders:
+        tup = ctx.mbe_tuples(norb, occ_h, exp, ref, n, skip)
+        eps, status, iters = ctx.casci_batch(h1, eri, occ, ref, e_ref, n, tup, opts)
+        inc = ctx.mbe_increments(n, tup, eps, out["tuples"], out["inc"]) if n == len(out["inc"]) + 1 \
+            else None
+        if inc is None:
+            raise MbeError("orders must be 1, 2, ..., n without gaps")
+        out["tuples"].append(tup)
+        out["eps"].append(eps)
+        out["status"].append(status)
+        out["iters"].append(iters)
+        out["inc"].append(inc)
+    e_order, e_total = ctx.mbe_total(out["inc"], e_phi, e_ref)
+    out["e_order"] = e_order
+    out["e_total"] = e_total
+    return out

@@ -1,0 +1,1476 @@
+// a2-a7: batched tuple CASCI.
+//
+// For every tuple Omega of the batch, with A = R u Omega (n orbitals) and
+// n_alpha = n_beta = k = |O n A|:
+//   a2  h_eff = F[A,A] - sum_{i in O n A} (2 (pq|ii) - (pi|iq)), F the core Fock
+//       matrix h + sum_{i in O}(2 J_i - K_i); V[(pq),(rs)] = (pq|rs) over A with
+//       symmetric pair packing; h'_pq = h_eff_pq - 1/2 sum_r (pr|rq);
+//   a3  the (n, k) string class tables (cached in the context);
+//   a4  the one-spin string Hamiltonian Hs = sum h'_pq E_pq + 1/2 sum (pq|rs)
+//       E_pq E_rs (an Ns x Ns matrix, identical for both spins because
+//       n_alpha = n_beta), the determinant diagonal
+//       H_II = Hs[Ia,Ia] + Hs[Ib,Ib] + sum_{p in Ia, q in Ib} (pp|qq),
+//       and the start vector (lowest diagonal element plus a small fixed
+//       pseudo-random admixture that reaches every symmetry sector);
+//   a5  sigma = H c = Hs C + C Hs^T + sum_{pq,rs} (pq|rs) E^a_pq E^b_rs C, the
+//       last term as a double loop over the alpha and beta replacement lists;
+//   a6  a block Davidson (locally optimal 3-vector form: current Ritz vector,
+//       previous direction, preconditioned residual) with the diagonal
+//       preconditioner, run in float32 first (mixed mode) and float64 last;
+//   a7  eps = lambda_min - H[Phi_A, Phi_A] - e_ref_corr.
+//
+// Two solvers: problems of <= 416 determinants run one per warp with the
+// Davidson vectors in registers (13 determinants per lane at most) and all
+// per-tuple data in shared memory; larger ones run one per thread block with
+// the vectors and Hs in a per-block slot of the context workspace.  Both are
+// persistent kernels that pull tuples from an atomic counter per bucket.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mbe {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int WARP_MAX_N = 8;
+constexpr int WARP_MAX_NDET = 416;
+constexpr int WARPS_PER_BLOCK = 4;
+constexpr int CTA_THREADS = 256;
+constexpr int MAX_BUCKETS = 8;
+constexpr int DPL_SET[5] = {1, 2, 4, 8, 13};
+
+struct ClassInfo {
+    const uint32_t *strings;
+    const int32_t *table;
+    int ns, r;
+};
+
+struct BatchArgs {
+    int norb, n, n_ref, order;
+    const double *eri;
+    const double *F;
+    const uint8_t *occ;
+    int ref[MBE_MAX_CAS];
+    const int32_t *tuples;
+    int64_t n_tuples;
+    const int32_t *perm;
+    const int64_t *bucket_off;
+    unsigned long long *counters;
+    ClassInfo cls[MBE_MAX_CAS + 1];
+    double e_ref_corr;
+    int precision;
+    double tol, tol_switch;
+    int max_iter, min_fp64;
+    double *eps;
+    int32_t *status;
+    int32_t *iters;
+    char *scratch;
+    size_t slot_bytes;
+};
+
+// ------------------------------------------------------------------ group primitives
+
+struct WarpGroup {
+    __device__ static int rank() { return threadIdx.x & 31; }
+    __device__ static int size() { return 32; }
+    __device__ static void sync() { __syncwarp(); }
+};
+
+struct BlockGroup {
+    __device__ static int rank() { return threadIdx.x; }
+    __device__ static int size() { return blockDim.x; }
+    __device__ static void sync() { __syncthreads(); }
+};
+
+template <typename T>
+__device__ inline T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Sum of K values over the block; every thread gets the totals.  red: >= 32*K.
+template <typename T, int K>
+__device__ inline void block_sum(T (&v)[K], T *red)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < K; ++i) v[i] = warp_sum(v[i]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < K; ++i) red[w * K + i] = v[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        T s = 0;
+        for (int j = 0; j < nw; ++j) s += red[j * K + i];
+        v[i] = s;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ per-tuple problem
+
+struct Problem {
+    int n, P, k, Ns, N, R, RS, HSS;
+    const uint32_t *str;  // [Ns]
+    const int32_t *tab;   // [Ns * RS]
+    const int *A;         // [n] global orbital indices
+    const short *pp;      // [2P] pair -> (p, q)
+    double *h;            // [n*n] h_eff, then scratch
+    double *hp;           // [P] h' packed
+    double *V64;          // [P*P]
+    float *V32;           // [P*P]
+    double *Hs64;         // [Ns*HSS]
+    float *Hs32;          // [Ns*HSS]
+    double *diag;         // [N]
+    void *c;              // [N] vector sigma reads (T)
+};
+
+__host__ __device__ inline int odd_stride(int x) { return x | 1; }
+
+__device__ inline size_t eri_index(int norb, int p, int q, int r, int s)
+{
+    return (((size_t)p * norb + q) * norb + r) * norb + s;
+}
+
+// A = ref u tuple_t (sorted merge).  Returns false for a malformed tuple.
+__device__ inline bool build_A(const BatchArgs &a, int64_t t, int *A)
+{
+    const int32_t *row = a.tuples ? a.tuples + t * a.order : nullptr;
+    int i = 0, j = 0, m = 0, prev = -1;
+    while (i < a.n_ref || j < a.order) {
+        int v;
+        if (j >= a.order || (i < a.n_ref && a.ref[i] < row[j])) {
+            v = a.ref[i++];
+        } else {
+            v = row[j++];
+            if (v < 0 || v >= a.norb) return false;
+        }
+        if (v <= prev) return false;  // unsorted, repeated or overlapping R
+        prev = v;
+        A[m++] = v;
+    }
+    return true;
+}
+
+// a2 + a4 set-up shared by both solvers.  Fills h_eff, V, h', Hs and the diagonal.
+template <class G>
+__device__ void setup_problem(const BatchArgs &a, Problem &pb, bool want32)
+{
+    const int tid = G::rank(), nt = G::size();
+    const int n = pb.n, P = pb.P, norb = a.norb;
+    // pair table
+    for (int e = tid; e < P; e += nt) {
+        int p = 0;
+        while ((p + 1) * (p + 2) / 2 <= e) ++p;
+        ((short *)pb.pp)[2 * e] = (short)p;
+        ((short *)pb.pp)[2 * e + 1] = (short)(e - p * (p + 1) / 2);
+    }
+    // h_eff from the core Fock matrix minus the in-space occupied orbitals
+    for (int e = tid; e < n * n; e += nt) {
+        int x = e / n, y = e - x * n;
+        int gp = pb.A[x], gq = pb.A[y];
+        double v = a.F[gp * norb + gq];
+        for (int c = 0; c < n; ++c) {
+            int gi = pb.A[c];
+            if (a.occ[gi])
+                v -= 2.0 * a.eri[eri_index(norb, gp, gq, gi, gi)] - a.eri[eri_index(norb, gp, gi, gi, gq)];
+        }
+        pb.h[e] = v;
+    }
+    G::sync();
+    // V over packed pairs
+    for (int e = tid; e < P * P; e += nt) {
+        int x = e / P, y = e - x * P;
+        int p = pb.pp[2 * x], q = pb.pp[2 * x + 1], r = pb.pp[2 * y], s = pb.pp[2 * y + 1];
+        double v = a.eri[eri_index(norb, pb.A[p], pb.A[q], pb.A[r], pb.A[s])];
+        pb.V64[e] = v;
+        if (want32) pb.V32[e] = (float)v;
+    }
+    G::sync();
+    // h'_pq = h_eff_pq - 1/2 sum_r (pr|rq)
+    for (int e = tid; e < P; e += nt) {
+        int p = pb.pp[2 * e], q = pb.pp[2 * e + 1];
+        double v = pb.h[p * n + q];
+        for (int r = 0; r < n; ++r) v -= 0.5 * pb.V64[pair_index(p, r) * P + pair_index(r, q)];
+        pb.hp[e] = v;
+    }
+    G::sync();
+    // Hs, one column J per thread:  <K|E_rs|J> = sb and <L|E_pq|K> = sa give
+    // Hs[K,J] += h'_rs sb  and  Hs[L,J] += 1/2 (pq|rs) sa sb.
+    for (int J = tid; J < pb.Ns; J += nt) {
+        for (int I = 0; I < pb.Ns; ++I) pb.Hs64[I * pb.HSS + J] = 0.0;
+        const int32_t *tj = pb.tab + J * pb.RS;
+        for (int b = 0; b < pb.R; ++b) {
+            int eb = tj[b];
+            int K = entry_J(eb), rs = entry_pair(eb);
+            double sb = entry_neg(eb) ? -1.0 : 1.0;
+            pb.Hs64[K * pb.HSS + J] += sb * pb.hp[rs];
+            const int32_t *tk = pb.tab + K * pb.RS;
+            for (int q = 0; q < pb.R; ++q) {
+                int ea = tk[q];
+                double sa = entry_neg(ea) ? -1.0 : 1.0;
+                pb.Hs64[entry_J(ea) * pb.HSS + J] += 0.5 * sa * sb * pb.V64[entry_pair(ea) * P + rs];
+            }
+        }
+    }
+    G::sync();
+    if (want32)
+        for (int e = tid; e < pb.Ns * pb.HSS; e += nt) pb.Hs32[e] = (float)pb.Hs64[e];
+    // diagonal
+    for (int d = tid; d < pb.N; d += nt) {
+        int ia = d / pb.Ns, ib = d - ia * pb.Ns;
+        double v = pb.Hs64[ia * pb.HSS + ia] + pb.Hs64[ib * pb.HSS + ib];
+        uint32_t sa = pb.str[ia];
+        while (sa) {
+            int p = __ffs((int)sa) - 1;
+            sa &= sa - 1;
+            uint32_t sb = pb.str[ib];
+            while (sb) {
+                int q = __ffs((int)sb) - 1;
+                sb &= sb - 1;
+                v += pb.V64[pair_index(p, p) * P + pair_index(q, q)];
+            }
+        }
+        pb.diag[d] = v;
+    }
+    G::sync();
+}
+
+// a5: one element of sigma = H c.
+template <typename T>
+__device__ inline T sigma_elem(const Problem &pb, const T *__restrict__ V, const T *__restrict__ Hs,
+                               const T *__restrict__ c, int d)
+{
+    const int Ns = pb.Ns;
+    int ia = d / Ns, ib = d - ia * Ns;
+    const T *ha = Hs + ia * pb.HSS;
+    const T *hb = Hs + ib * pb.HSS;
+    const T *crow = c + ia * Ns;
+    T acc = 0;
+    for (int J = 0; J < Ns; ++J) acc += ha[J] * c[J * Ns + ib] + hb[J] * crow[J];
+    const int32_t *ta = pb.tab + ia * pb.RS;
+    const int32_t *tb = pb.tab + ib * pb.RS;
+    for (int x = 0; x < pb.R; ++x) {
+        int ea = ta[x];
+        const T *vrow = V + entry_pair(ea) * pb.P;
+        const T *cr = c + entry_J(ea) * Ns;
+        T s = 0;
+        for (int y = 0; y < pb.R; ++y) {
+            int eb = tb[y];
+            T v = vrow[entry_pair(eb)] * cr[entry_J(eb)];
+            s = entry_neg(eb) ? s - v : s + v;
+        }
+        acc = entry_neg(ea) ? acc - s : acc + s;
+    }
+    return acc;
+}
+
+// Lowest eigenpair of the symmetric 3x3 Rayleigh-Ritz matrix G (m = 2 or 3 active
+// rows; with m = 2 the middle row/column is absent).  Float32 Jacobi on G shifted
+// by G00, then (float64 phase) one inverse-iteration step in float64.
+__device__ inline void rotate3(float (&A)[3][3], float (&Vv)[3][3], int p, int q)
+{
+    float apq = A[p][q];
+    if (apq == 0.0f) return;
+    float theta = (A[q][q] - A[p][p]) / (2.0f * apq);
+    float t = 1.0f / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+    if (theta < 0.0f) t = -t;
+    float c = rsqrtf(t * t + 1.0f), s = t * c;
+    A[p][p] -= t * apq;
+    A[q][q] += t * apq;
+    A[p][q] = A[q][p] = 0.0f;
+    int r = 3 - p - q;
+    float arp = A[r][p], arq = A[r][q];
+    A[r][p] = A[p][r] = c * arp - s * arq;
+    A[r][q] = A[q][r] = s * arp + c * arq;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float vp = Vv[i][p], vq = Vv[i][q];
+        Vv[i][p] = c * vp - s * vq;
+        Vv[i][q] = s * vp + c * vq;
+    }
+}
+
+template <typename T>
+__device__ inline void eig3(const T (&G)[3][3], bool have_p, T (&y)[3])
+{
+    float A[3][3], Vv[3][3];
+    const T s0 = G[0][0];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            A[i][j] = (float)(G[i][j] - (i == j ? s0 : (T)0));
+            Vv[i][j] = (i == j) ? 1.0f : 0.0f;
+        }
+    if (!have_p) {
+        A[0][1] = A[1][0] = A[1][2] = A[2][1] = 0.0f;
+        A[1][1] = 3.0e30f;
+    }
+    for (int sweep = 0; sweep < 6; ++sweep) {
+        float off = fabsf(A[0][1]) + fabsf(A[0][2]) + fabsf(A[1][2]);
+        float dia = fabsf(A[0][0]) + fabsf(A[1][1]) + fabsf(A[2][2]);
+        if (off <= 1e-10f * dia || off < 1e-36f) break;
+        rotate3(A, Vv, 0, 1);
+        rotate3(A, Vv, 0, 2);
+        rotate3(A, Vv, 1, 2);
+    }
+    int m = 0;
+    if (A[1][1] < A[m][m]) m = 1;
+    if (A[2][2] < A[m][m]) m = 2;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[i] = (T)Vv[i][m];
+    if (!have_p) y[1] = (T)0;
+    if constexpr (sizeof(T) == 8) {
+        // float64 phase: one inverse-iteration step z = adj(G - theta I) y with
+        // theta = y^T G y / y^T y makes the float32 eigenvector float64-accurate.
+        T nrm = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+        T Gm[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Gm[i][j] = G[i][j];
+        if (!have_p) {
+            Gm[0][1] = Gm[1][0] = Gm[1][2] = Gm[2][1] = (T)0;
+            Gm[1][1] = G[0][0] + (T)1.0e30;
+        }
+        T th = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) th += y[i] * Gm[i][j] * y[j];
+        th /= nrm;
+        T M[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) M[i][j] = Gm[i][j] - (i == j ? th : (T)0);
+        T adj[3][3];
+        adj[0][0] = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+        adj[0][1] = M[0][2] * M[2][1] - M[0][1] * M[2][2];
+        adj[0][2] = M[0][1] * M[1][2] - M[0][2] * M[1][1];
+        adj[1][0] = M[1][2] * M[2][0] - M[1][0] * M[2][2];
+        adj[1][1] = M[0][0] * M[2][2] - M[0][2] * M[2][0];
+        adj[1][2] = M[0][2] * M[1][0] - M[0][0] * M[1][2];
+        adj[2][0] = M[1][0] * M[2][1] - M[1][1] * M[2][0];
+        adj[2][1] = M[0][1] * M[2][0] - M[0][0] * M[2][1];
+        adj[2][2] = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+        T z[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) z[i] = adj[i][0] * y[0] + adj[i][1] * y[1] + adj[i][2] * y[2];
+        T zz = z[0] * z[0] + z[1] * z[1] + z[2] * z[2];
+        if (zz > (T)1e-280 && isfinite(zz)) {
+            T inv = (T)1 / sqrt(zz);
+            T sgn = (z[0] * y[0] + z[1] * y[1] + z[2] * y[2]) < (T)0 ? -inv : inv;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) y[i] = z[i] * sgn;
+        } else {
+            T inv = (T)1 / sqrt(nrm);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) y[i] *= inv;
+        }
+        if (!have_p) y[1] = (T)0;
+    }
+}
+
+// Fixed pseudo-random admixture of the start vector, in [-1, 1].
+__device__ inline double guess_noise(int d)
+{
+    uint32_t h = (uint32_t)d * 2654435761u + 0x9e3779b9u;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    return (double)(h & 0xffffu) / 32768.0 - 1.0;
+}
+
+constexpr double GUESS_NOISE = 1e-2;
+
+struct PhaseOut {
+    double lambda, rnorm;
+    int nsig, status;
+};
+
+// ------------------------------------------------------------------ warp solver
+
+template <typename T, int DPL>
+__device__ inline void sigma_warp(const Problem &pb, const T *V, const T *Hs, const T *c, T (&out)[DPL])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < DPL; ++j) {
+        int d = lane + 32 * j;
+        out[j] = (d < pb.N) ? sigma_elem<T>(pb, V, Hs, c, d) : (T)0;
+    }
+}
+
+template <typename T>
+__device__ inline T tiny_norm();
+template <>
+__device__ inline float tiny_norm<float>() { return 1e-6f; }
+template <>
+__device__ inline double tiny_norm<double>() { return 1e-13; }
+
+// One Davidson phase in precision T.  x: start vector (any norm) in, Ritz vector out.
+template <typename T, int DPL>
+__device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, int min_iter,
+                                  int max_iter, bool steer)
+{
+    const int lane = threadIdx.x & 31;
+    const T *V = sizeof(T) == 8 ? (const T *)pb.V64 : (const T *)pb.V32;
+    const T *Hs = sizeof(T) == 8 ? (const T *)pb.Hs64 : (const T *)pb.Hs32;
+    T *c = (T *)pb.c;
+    T hx[DPL], p[DPL], hp[DPL], ht[DPL];
+    PhaseOut o;
+    o.nsig = 0;
+    o.status = MBE_STATUS_OK;
+
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < DPL; ++j) s += x[j] * x[j];
+    s = warp_sum(s);
+    T inv = (T)1 / sqrt(s);
+#pragma unroll
+    for (int j = 0; j < DPL; ++j) {
+        x[j] *= inv;
+        int d = lane + 32 * j;
+        if (d < pb.N) c[d] = x[j];
+        p[j] = 0;
+        hp[j] = 0;
+    }
+    __syncwarp();
+    sigma_warp<T, DPL>(pb, V, Hs, c, hx);
+    ++o.nsig;
+    __syncwarp();
+    T xh = 0;
+#pragma unroll
+    for (int j = 0; j < DPL; ++j) xh += x[j] * hx[j];
+    T lam = warp_sum(xh);
+    bool have_p = false;
+    T best = (T)3e38;
+    int stall = 0;
+    T rn = 0;
+    for (int it = 0;; ++it) {
+        T rr = 0;
+#pragma unroll
+        for (int j = 0; j < DPL; ++j) {
+            int d = lane + 32 * j;
+            if (d < pb.N) {
+                T r = hx[j] - lam * x[j];
+                rr += r * r;
+                T den = (T)pb.diag[d] - lam;
+                if (fabs(den) < (T)1e-4) den = den >= (T)0 ? (T)1e-4 : (T)-1e-4;
+                c[d] = r / den;
+            }
+        }
+        rn = sqrt(warp_sum(rr));
+        if (!isfinite(rn) || !isfinite(lam)) {
+            o.status = MBE_STATUS_NONFINITE;
+            break;
+        }
+        if (rn <= (T)tol && it >= min_iter) break;
+        if (it >= max_iter) {
+            o.status = MBE_STATUS_MAXITER;
+            break;
+        }
+        if (steer) {
+            if (rn < (T)0.9 * best) {
+                best = rn;
+                stall = 0;
+            } else if (++stall >= 3) {
+                break;
+            }
+        }
+        // orthonormalise t against x and p (two passes)
+        for (int pass = 0; pass < 2; ++pass) {
+            T ax = 0, ap = 0;
+#pragma unroll
+            for (int j = 0; j < DPL; ++j) {
+                int d = lane + 32 * j;
+                if (d < pb.N) {
+                    ax += x[j] * c[d];
+                    ap += p[j] * c[d];
+                }
+            }
+            ax = warp_sum(ax);
+            ap = warp_sum(ap);
+#pragma unroll
+            for (int j = 0; j < DPL; ++j) {
+                int d = lane + 32 * j;
+                if (d < pb.N) c[d] -= ax * x[j] + ap * p[j];
+            }
+        }
+        T tt = 0;
+#pragma unroll
+        for (int j = 0; j < DPL; ++j) {
+            int d = lane + 32 * j;
+            if (d < pb.N) tt += c[d] * c[d];
+        }
+        T tn = sqrt(warp_sum(tt));
+        if (!(tn > tiny_norm<T>())) {
+            // The correction lies in span{x, p}: nothing left to add.
+            if (!steer && rn > (T)tol) o.status = MBE_STATUS_MAXITER;
+            break;
+        }
+        T tinv = (T)1 / tn;
+#pragma unroll
+        for (int j = 0; j < DPL; ++j) {
+            int d = lane + 32 * j;
+            if (d < pb.N) c[d] *= tinv;
+        }
+        __syncwarp();
+        sigma_warp<T, DPL>(pb, V, Hs, c, ht);
+        ++o.nsig;
+        __syncwarp();
+        T g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0;
+#pragma unroll
+        for (int j = 0; j < DPL; ++j) {
+            int d = lane + 32 * j;
+            T tj = (d < pb.N) ? c[d] : (T)0;
+            g00 += x[j] * hx[j];
+            g01 += x[j] * hp[j];
+            g02 += x[j] * ht[j];
+            g11 += p[j] * hp[j];
+            g12 += p[j] * ht[j];
+            g22 += tj * ht[j];
+        }
+        T G[3][3];
+        G[0][0] = warp_sum(g00);
+        G[0][1] = G[1][0] = warp_sum(g01);
+        G[0][2] = G[2][0] = warp_sum(g02);
+        G[1][1] = warp_sum(g11);
+        G[1][2] = G[2][1] = warp_sum(g12);
+        G[2][2] = warp_sum(g22);
+        T y[3];
+        eig3<T>(G, have_p, y);
+        T w2 = y[1] * y[1] + y[2] * y[2];
+        T q0 = -w2 * y[0], q1 = y[1] - w2 * y[1], q2 = y[2] - w2 * y[2];
+        T zn = sqrt(q0 * q0 + q1 * q1 + q2 * q2);
+        bool np_ok = zn > tiny_norm<T>() * (T)1e-3;
+        T zi = np_ok ? (T)1 / zn : (T)0;
+        T y0 = y[0], y1 = y[1], y2 = y[2];
+        q0 *= zi;
+        q1 *= zi;
+        q2 *= zi;
+        T xx = 0, xhx = 0;
+#pragma unroll
+        for (int j = 0; j < DPL; ++j) {
+            int d = lane + 32 * j;
+            T tj = (d < pb.N) ? c[d] : (T)0;
+            T nx = y0 * x[j] + y1 * p[j] + y2 * tj;
+            T nhx = y0 * hx[j] + y1 * hp[j] + y2 * ht[j];
+            T npv = q0 * x[j] + q1 * p[j] + q2 * tj;
+            T nhp = q0 * hx[j] + q1 * hp[j] + q2 * ht[j];
+            x[j] = nx;
+            hx[j] = nhx;
+            p[j] = npv;
+            hp[j] = nhp;
+            xx += nx * nx;
+            xhx += nx * nhx;
+        }
+        have_p = np_ok;
+        xx = warp_sum(xx);
+        xhx = warp_sum(xhx);
+        T xi = (T)1 / sqrt(xx);
+#pragma unroll
+        for (int j = 0; j < DPL; ++j) {
+            x[j] *= xi;
+            hx[j] *= xi;
+        }
+        lam = xhx / xx;
+        __syncwarp();
+    }
+    o.lambda = (double)lam;
+    o.rnorm = (double)rn;
+    return o;
+}
+
+struct WarpLayout {
+    int off_A, off_pp, off_h, off_hp, off_V64, off_V32, off_Hs64, off_Hs32, off_diag, off_c, off_str,
+        off_tab, bytes;
+};
+
+__host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
+
+__host__ __device__ inline WarpLayout warp_layout(int n, int ns, int r, int N)
+{
+    WarpLayout L;
+    int P = n * (n + 1) / 2, HSS = odd_stride(ns), RS = odd_stride(r > 0 ? r : 1);
+    int o = 0;
+    L.off_A = o; o = al16(o + 4 * MBE_MAX_CAS);
+    L.off_pp = o; o = al16(o + 4 * P);
+    L.off_h = o; o = al16(o + 8 * n * n);
+    L.off_hp = o; o = al16(o + 8 * P);
+    L.off_V64 = o; o = al16(o + 8 * P * P);
+    L.off_V32 = o; o = al16(o + 4 * P * P);
+    L.off_Hs64 = o; o = al16(o + 8 * ns * HSS);
+    L.off_Hs32 = o; o = al16(o + 4 * ns * HSS);
+    L.off_diag = o; o = al16(o + 8 * N);
+    L.off_c = o; o = al16(o + 8 * N);
+    L.off_str = o; o = al16(o + 4 * ns);
+    L.off_tab = o; o = al16(o + 4 * ns * RS);
+    L.bytes = o;
+    return L;
+}
+
+__device__ inline void store_result(const BatchArgs &a, int64_t t, double eps, int status, int n64, int n32)
+{
+    a.eps[t] = eps;
+    a.status[t] = status;
+    if (a.iters) a.iters[t] = (n64 << 16) | (n32 & 0xffff);
+}
+
+template <int DPL>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
+    k_casci_warp(BatchArgs a, int bucket, WarpLayout L)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    char *ws = smem + (size_t)wib * L.bytes;
+    const int64_t begin = a.bucket_off[bucket];
+    const int64_t cnt = a.bucket_off[bucket + 1] - begin;
+    const int n = a.n, P = n * (n + 1) / 2;
+    int *A = (int *)(ws + L.off_A);
+    for (;;) {
+        unsigned long long pos = 0;
+        if (lane == 0) pos = atomicAdd(&a.counters[bucket], 1ULL);
+        pos = __shfl_sync(FULL, pos, 0);
+        if ((int64_t)pos >= cnt) break;
+        const int64_t t = a.perm[begin + (int64_t)pos];
+        if (lane == 0) build_A(a, t, A);
+        __syncwarp();
+        int k = 0;
+        for (int i = 0; i < n; ++i) k += a.occ[A[i]];
+        const ClassInfo ci = a.cls[k];
+        Problem pb;
+        pb.n = n;
+        pb.P = P;
+        pb.k = k;
+        pb.Ns = ci.ns;
+        pb.N = ci.ns * ci.ns;
+        pb.R = ci.r;
+        pb.RS = odd_stride(ci.r > 0 ? ci.r : 1);
+        pb.HSS = odd_stride(ci.ns);
+        uint32_t *str = (uint32_t *)(ws + L.off_str);
+        int32_t *tab = (int32_t *)(ws + L.off_tab);
+        for (int i = lane; i < ci.ns; i += 32) str[i] = ci.strings[i];
+        for (int i = lane; i < ci.ns * ci.r; i += 32) {
+            int row = i / ci.r, col = i - row * ci.r;
+            tab[row * pb.RS + col] = ci.table[i];
+        }
+        pb.str = str;
+        pb.tab = tab;
+        pb.A = A;
+        pb.pp = (const short *)(ws + L.off_pp);
+        pb.h = (double *)(ws + L.off_h);
+        pb.hp = (double *)(ws + L.off_hp);
+        pb.V64 = (double *)(ws + L.off_V64);
+        pb.V32 = (float *)(ws + L.off_V32);
+        pb.Hs64 = (double *)(ws + L.off_Hs64);
+        pb.Hs32 = (float *)(ws + L.off_Hs32);
+        pb.diag = (double *)(ws + L.off_diag);
+        pb.c = (void *)(ws + L.off_c);
+        __syncwarp();
+        const bool mixed = a.precision == MBE_PREC_MIXED;
+        setup_problem<WarpGroup>(a, pb, mixed);
+        // Phi_A: the in-space occupied orbitals
+        uint32_t mphi = 0;
+        for (int i = 0; i < n; ++i)
+            if (a.occ[A[i]]) mphi |= 1u << i;
+        int iphi = string_rank(mphi);
+        double ephi = pb.diag[iphi * pb.Ns + iphi];
+        if (pb.N == 1) {
+            if (lane == 0) store_result(a, t, pb.diag[0] - ephi - a.e_ref_corr, MBE_STATUS_OK, 0, 0);
+            __syncwarp();
+            continue;
+        }
+        // start vector: lowest diagonal element (ties -> lowest index) + fixed admixture
+        double best = 1e300;
+        int bi = 0x7fffffff;
+        for (int d = lane; d < pb.N; d += 32) {
+            double v = pb.diag[d];
+            if (v < best || (v == best && d < bi)) {
+                best = v;
+                bi = d;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(FULL, best, o);
+            int oi = __shfl_xor_sync(FULL, bi, o);
+            if (ov < best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+        }
+        double x64[DPL];
+#pragma unroll
+        for (int j = 0; j < DPL; ++j) {
+            int d = lane + 32 * j;
+            x64[j] = (d < pb.N) ? ((d == bi ? 1.0 : 0.0) + GUESS_NOISE * guess_noise(d)) : 0.0;
+        }
+        int n32 = 0;
+        if (mixed) {
+            float x32[DPL];
+#pragma unroll
+            for (int j = 0; j < DPL; ++j) x32[j] = (float)x64[j];
+            PhaseOut o32 = davidson_warp<float, DPL>(pb, x32, a.tol_switch, 0, a.max_iter, true);
+            n32 = o32.nsig;
+            if (o32.status != MBE_STATUS_NONFINITE)
+#pragma unroll
+                for (int j = 0; j < DPL; ++j) x64[j] = (double)x32[j];
+        }
+        PhaseOut o64 = davidson_warp<double, DPL>(pb, x64, a.tol, mixed ? a.min_fp64 : 0, a.max_iter, false);
+        if (lane == 0) {
+            double e = o64.status == MBE_STATUS_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL)
+                                                         : o64.lambda - ephi - a.e_ref_corr;
+            store_result(a, t, e, o64.status, o64.nsig, n32);
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ block solver
+
+// Per-block workspace slot: vectors and Hs in global memory.
+struct SlotLayout {
+    size_t off_x, off_hx, off_p, off_hp, off_t, off_ht, off_diag, off_Hs64, off_Hs32, bytes;
+};
+
+__host__ __device__ inline SlotLayout slot_layout(int ns, int N)
+{
+    SlotLayout L;
+    size_t o = 0;
+    size_t vec = ((size_t)N * 8 + 255) & ~(size_t)255;
+    int HSS = odd_stride(ns);
+    L.off_x = o; o += vec;
+    L.off_hx = o; o += vec;
+    L.off_p = o; o += vec;
+    L.off_hp = o; o += vec;
+    L.off_t = o; o += vec;
+    L.off_ht = o; o += vec;
+    L.off_diag = o; o += vec;
+    L.off_Hs64 = o; o += ((size_t)ns * HSS * 8 + 255) & ~(size_t)255;
+    L.off_Hs32 = o; o += ((size_t)ns * HSS * 4 + 255) & ~(size_t)255;
+    L.bytes = o;
+    return L;
+}
+
+struct BlockSmem {  // dynamic shared memory of the block solver
+    int off_A, off_pp, off_h, off_hp, off_V64, off_V32, off_red, bytes;
+};
+
+__host__ __device__ inline BlockSmem block_smem(int n)
+{
+    BlockSmem S;
+    int P = n * (n + 1) / 2, o = 0;
+    S.off_A = o; o = al16(o + 4 * MBE_MAX_CAS);
+    S.off_pp = o; o = al16(o + 4 * P);
+    S.off_h = o; o = al16(o + 8 * n * n);
+    S.off_hp = o; o = al16(o + 8 * P);
+    S.off_V64 = o; o = al16(o + 8 * P * P);
+    S.off_V32 = o; o = al16(o + 4 * P * P);
+    S.off_red = o; o = al16(o + 8 * 32 * 8);
+    S.bytes = o;
+    return S;
+}
+
+template <typename T>
+__device__ PhaseOut davidson_block(const Problem &pb, T *x, T *hx, T *p, T *hp, T *t, T *ht, double *red,
+                                   double tol, int min_iter, int max_iter, bool steer)
+{
+    const int tid = threadIdx.x, nt = blockDim.x, N = pb.N;
+    const T *V = sizeof(T) == 8 ? (const T *)pb.V64 : (const T *)pb.V32;
+    const T *Hs = sizeof(T) == 8 ? (const T *)pb.Hs64 : (const T *)pb.Hs32;
+    T *tred = (T *)red;
+    PhaseOut o;
+    o.nsig = 0;
+    o.status = MBE_STATUS_OK;
+    {
+        T v[1] = {0};
+        for (int d = tid; d < N; d += nt) v[0] += x[d] * x[d];
+        block_sum<T, 1>(v, tred);
+        T inv = (T)1 / sqrt(v[0]);
+        for (int d = tid; d < N; d += nt) {
+            x[d] *= inv;
+            p[d] = 0;
+            hp[d] = 0;
+        }
+    }
+    __syncthreads();
+    for (int d = tid; d < N; d += nt) hx[d] = sigma_elem<T>(pb, V, Hs, x, d);
+    ++o.nsig;
+    T lam;
+    {
+        T v[1] = {0};
+        for (int d = tid; d < N; d += nt) v[0] += x[d] * hx[d];
+        block_sum<T, 1>(v, tred);
+        lam = v[0];
+    }
+    bool have_p = false;
+    T best = (T)3e38, rn = 0;
+    int stall = 0;
+    for (int it = 0;; ++it) {
+        T v1[1] = {0};
+        for (int d = tid; d < N; d += nt) {
+            T r = hx[d] - lam * x[d];
+            v1[0] += r * r;
+            T den = (T)pb.diag[d] - lam;
+            if (fabs(den) < (T)1e-4) den = den >= (T)0 ? (T)1e-4 : (T)-1e-4;
+            t[d] = r / den;
+        }
+        block_sum<T, 1>(v1, tred);
+        rn = sqrt(v1[0]);
+        if (!isfinite(rn) || !isfinite(lam)) {
+            o.status = MBE_STATUS_NONFINITE;
+            break;
+        }
+        if (rn <= (T)tol && it >= min_iter) break;
+        if (it >= max_iter) {
+            o.status = MBE_STATUS_MAXITER;
+            break;
+        }
+        if (steer) {
+            if (rn < (T)0.9 * best) {
+                best = rn;
+                stall = 0;
+            } else if (++stall >= 3) {
+                break;
+            }
+        }
+        for (int pass = 0; pass < 2; ++pass) {
+            T v2[2] = {0, 0};
+            for (int d = tid; d < N; d += nt) {
+                v2[0] += x[d] * t[d];
+                v2[1] += p[d] * t[d];
+            }
+            block_sum<T, 2>(v2, tred);
+            for (int d = tid; d < N; d += nt) t[d] -= v2[0] * x[d] + v2[1] * p[d];
+        }
+        T v3[1] = {0};
+        for (int d = tid; d < N; d += nt) v3[0] += t[d] * t[d];
+        block_sum<T, 1>(v3, tred);
+        T tn = sqrt(v3[0]);
+        if (!(tn > tiny_norm<T>())) {
+            if (!steer && rn > (T)tol) o.status = MBE_STATUS_MAXITER;
+            break;
+        }
+        T tinv = (T)1 / tn;
+        for (int d = tid; d < N; d += nt) t[d] *= tinv;
+        __syncthreads();
+        for (int d = tid; d < N; d += nt) ht[d] = sigma_elem<T>(pb, V, Hs, t, d);
+        ++o.nsig;
+        T g[6] = {0, 0, 0, 0, 0, 0};
+        for (int d = tid; d < N; d += nt) {
+            g[0] += x[d] * hx[d];
+            g[1] += x[d] * hp[d];
+            g[2] += x[d] * ht[d];
+            g[3] += p[d] * hp[d];
+            g[4] += p[d] * ht[d];
+            g[5] += t[d] * ht[d];
+        }
+        block_sum<T, 6>(g, tred);
+        T G[3][3];
+        G[0][0] = g[0];
+        G[0][1] = G[1][0] = g[1];
+        G[0][2] = G[2][0] = g[2];
+        G[1][1] = g[3];
+        G[1][2] = G[2][1] = g[4];
+        G[2][2] = g[5];
+        T y[3];
+        eig3<T>(G, have_p, y);
+        T w2 = y[1] * y[1] + y[2] * y[2];
+        T q0 = -w2 * y[0], q1 = y[1] - w2 * y[1], q2 = y[2] - w2 * y[2];
+        T zn = sqrt(q0 * q0 + q1 * q1 + q2 * q2);
+        bool np_ok = zn > tiny_norm<T>() * (T)1e-3;
+        T zi = np_ok ? (T)1 / zn : (T)0;
+        T y0 = y[0], y1 = y[1], y2 = y[2];
+        q0 *= zi;
+        q1 *= zi;
+        q2 *= zi;
+        T v4[2] = {0, 0};
+        for (int d = tid; d < N; d += nt) {
+            T xd = x[d], pd = p[d], td = t[d], hxd = hx[d], hpd = hp[d], htd = ht[d];
+            T nx = y0 * xd + y1 * pd + y2 * td;
+            T nhx = y0 * hxd + y1 * hpd + y2 * htd;
+            x[d] = nx;
+            hx[d] = nhx;
+            p[d] = q0 * xd + q1 * pd + q2 * td;
+            hp[d] = q0 * hxd + q1 * hpd + q2 * htd;
+            v4[0] += nx * nx;
+            v4[1] += nx * nhx;
+        }
+        have_p = np_ok;
+        block_sum<T, 2>(v4, tred);
+        T xi = (T)1 / sqrt(v4[0]);
+        for (int d = tid; d < N; d += nt) {
+            x[d] *= xi;
+            hx[d] *= xi;
+        }
+        lam = v4[1] / v4[0];
+        __syncthreads();
+    }
+    o.lambda = (double)lam;
+    o.rnorm = (double)rn;
+    return o;
+}
+
+__global__ void __launch_bounds__(CTA_THREADS) k_casci_block(BatchArgs a, int bucket)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int n = a.n, P = n * (n + 1) / 2;
+    const BlockSmem S = block_smem(n);
+    int *A = (int *)(smem + S.off_A);
+    double *red = (double *)(smem + S.off_red);
+    __shared__ unsigned long long s_pos;
+    char *slot = a.scratch + (size_t)blockIdx.x * a.slot_bytes;
+    const int64_t begin = a.bucket_off[bucket];
+    const int64_t cnt = a.bucket_off[bucket + 1] - begin;
+    for (;;) {
+        if (threadIdx.x == 0) s_pos = atomicAdd(&a.counters[bucket], 1ULL);
+        __syncthreads();
+        unsigned long long pos = s_pos;
+        __syncthreads();
+        if ((int64_t)pos >= cnt) break;
+        const int64_t t = a.perm[begin + (int64_t)pos];
+        if (threadIdx.x == 0) build_A(a, t, A);
+        __syncthreads();
+        int k = 0;
+        for (int i = 0; i < n; ++i) k += a.occ[A[i]];
+        const ClassInfo ci = a.cls[k];
+        Problem pb;
+        pb.n = n;
+        pb.P = P;
+        pb.k = k;
+        pb.Ns = ci.ns;
+        pb.N = ci.ns * ci.ns;
+        pb.R = ci.r;
+        pb.RS = ci.r;
+        pb.HSS = odd_stride(ci.ns);
+        pb.str = ci.strings;
+        pb.tab = ci.table;
+        pb.A = A;
+        pb.pp = (const short *)(smem + S.off_pp);
+        pb.h = (double *)(smem + S.off_h);
+        pb.hp = (double *)(smem + S.off_hp);
+        pb.V64 = (double *)(smem + S.off_V64);
+        pb.V32 = (float *)(smem + S.off_V32);
+        SlotLayout L = slot_layout(ci.ns, pb.N);
+        pb.Hs64 = (double *)(slot + L.off_Hs64);
+        pb.Hs32 = (float *)(slot + L.off_Hs32);
+        pb.diag = (double *)(slot + L.off_diag);
+        const bool mixed = a.precision == MBE_PREC_MIXED;
+        setup_problem<BlockGroup>(a, pb, mixed);
+        uint32_t mphi = 0;
+        for (int i = 0; i < n; ++i)
+            if (a.occ[A[i]]) mphi |= 1u << i;
+        int iphi = string_rank(mphi);
+        double ephi = pb.diag[iphi * pb.Ns + iphi];
+        if (pb.N == 1) {
+            if (threadIdx.x == 0) store_result(a, t, pb.diag[0] - ephi - a.e_ref_corr, MBE_STATUS_OK, 0, 0);
+            __syncthreads();
+            continue;
+        }
+        // argmin of the diagonal (ties -> lowest index)
+        double best = 1e300;
+        int bi = 0x7fffffff;
+        for (int d = threadIdx.x; d < pb.N; d += blockDim.x) {
+            double v = pb.diag[d];
+            if (v < best || (v == best && d < bi)) {
+                best = v;
+                bi = d;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(FULL, best, o);
+            int oi = __shfl_xor_sync(FULL, bi, o);
+            if (ov < best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[threadIdx.x >> 5] = best;
+            ((int *)(red + 32))[threadIdx.x >> 5] = bi;
+        }
+        __syncthreads();
+        best = red[0];
+        bi = ((int *)(red + 32))[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            double ov = red[w];
+            int oi = ((int *)(red + 32))[w];
+            if (ov < best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+        }
+        __syncthreads();
+        double *x64 = (double *)(slot + L.off_x);
+        for (int d = threadIdx.x; d < pb.N; d += blockDim.x)
+            x64[d] = (d == bi ? 1.0 : 0.0) + GUESS_NOISE * guess_noise(d);
+        __syncthreads();
+        int n32 = 0;
+        if (mixed) {
+            float *x32 = (float *)(slot + L.off_x);
+            // float views of the same slot: x in the first half of the x region
+            for (int base = 0; base < pb.N; base += blockDim.x) {
+                int d = base + threadIdx.x;
+                double v = (d < pb.N) ? x64[d] : 0.0;
+                __syncthreads();
+                if (d < pb.N) x32[d] = (float)v;
+                __syncthreads();
+            }
+            PhaseOut o32 = davidson_block<float>(
+                pb, x32, (float *)(slot + L.off_hx), (float *)(slot + L.off_p), (float *)(slot + L.off_hp),
+                (float *)(slot + L.off_t), (float *)(slot + L.off_ht), red, a.tol_switch, 0, a.max_iter, true);
+            n32 = o32.nsig;
+            // widen x back to float64 in place, from the top down
+            for (int base = ((pb.N - 1) / (int)blockDim.x) * (int)blockDim.x; base >= 0; base -= (int)blockDim.x) {
+                int d = base + threadIdx.x;
+                float v = (d < pb.N) ? x32[d] : 0.0f;
+                __syncthreads();
+                if (d < pb.N) x64[d] = (o32.status == MBE_STATUS_NONFINITE) ? 0.0 : (double)v;
+                __syncthreads();
+            }
+            if (o32.status == MBE_STATUS_NONFINITE) {
+                for (int d = threadIdx.x; d < pb.N; d += blockDim.x)
+                    x64[d] = (d == bi ? 1.0 : 0.0) + GUESS_NOISE * guess_noise(d);
+                __syncthreads();
+            }
+        }
+        pb.c = nullptr;
+        PhaseOut o64 = davidson_block<double>(
+            pb, x64, (double *)(slot + L.off_hx), (double *)(slot + L.off_p), (double *)(slot + L.off_hp),
+            (double *)(slot + L.off_t), (double *)(slot + L.off_ht), red, a.tol, mixed ? a.min_fp64 : 0,
+            a.max_iter, false);
+        if (threadIdx.x == 0) {
+            double e = o64.status == MBE_STATUS_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL)
+                                                         : o64.lambda - ephi - a.e_ref_corr;
+            store_result(a, t, e, o64.status, o64.nsig, n32);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ batch plumbing
+
+// F = h + sum_{i in O} (2 (pq|ii) - (pi|iq))
+__global__ void k_core_fock(int norb, const double *h1, const double *eri, const uint8_t *occ, double *F)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= norb * norb) return;
+    int p = e / norb, q = e - p * norb;
+    double v = h1[e];
+    for (int i = 0; i < norb; ++i)
+        if (occ[i]) v += 2.0 * eri[eri_index(norb, p, q, i, i)] - eri[eri_index(norb, p, i, i, q)];
+    F[e] = v;
+}
+
+struct ClassifyArgs {
+    int bucket_of_k[MBE_MAX_CAS + 1];
+    int nbuckets;
+};
+
+__global__ void k_classify(BatchArgs a, ClassifyArgs c, int32_t *key, int64_t *counts)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n_tuples) return;
+    int A[MBE_MAX_CAS];
+    int b = -1;
+    if (build_A(a, t, A)) {
+        int k = 0;
+        for (int i = 0; i < a.n; ++i) k += a.occ[A[i]];
+        b = c.bucket_of_k[k];
+    }
+    key[t] = b;
+    if (b < 0) {
+        a.eps[t] = __longlong_as_double(0x7ff8000000000000LL);
+        a.status[t] = MBE_STATUS_BADINPUT;
+        if (a.iters) a.iters[t] = 0;
+        return;
+    }
+    atomicAdd((unsigned long long *)&counts[b], 1ULL);
+}
+
+__global__ void k_scatter(int64_t n_tuples, int nbuckets, const int32_t *key, const int64_t *counts,
+                          unsigned long long *cursor, int64_t *bucket_off, int32_t *perm)
+{
+    __shared__ int64_t off[MAX_BUCKETS + 1];
+    if (threadIdx.x == 0) {
+        int64_t s = 0;
+        for (int b = 0; b < nbuckets; ++b) {
+            off[b] = s;
+            s += counts[b];
+        }
+        off[nbuckets] = s;
+        if (blockIdx.x == 0)
+            for (int b = 0; b <= nbuckets; ++b) bucket_off[b] = off[b];
+    }
+    __syncthreads();
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tuples) return;
+    int b = key[t];
+    if (b < 0) return;
+    unsigned long long slot = atomicAdd(&cursor[b], 1ULL);
+    perm[off[b] + (int64_t)slot] = (int32_t)t;
+}
+
+// Optional event pair around one solver launch (mbe_ctx_set_timing).
+struct TimedLaunch {
+    mbe_ctx *ctx;
+    mbe_ctx::Pending p;
+    bool on;
+    TimedLaunch(mbe_ctx *c, int order, int solver, int dpl) : ctx(c), on(c->timing)
+    {
+        if (!on) return;
+        p.rec.order = order;
+        p.rec.solver = solver;
+        p.rec.dpl = dpl;
+        p.rec.ms = 0.0f;
+        if (cudaEventCreate(&p.start) != cudaSuccess || cudaEventCreate(&p.stop) != cudaSuccess) {
+            on = false;
+            return;
+        }
+        cudaEventRecord(p.start, ctx->stream);
+    }
+    int done()
+    {
+        if (!on) return MBE_OK;
+        MBE_CU(cudaEventRecord(p.stop, ctx->stream));
+        ctx->pending.push_back(p);
+        return MBE_OK;
+    }
+};
+
+struct Bucket {
+    bool warp;
+    int dpl;
+    int max_ns, max_r, max_n;
+};
+
+template <int DPL>
+static int launch_warp(mbe_ctx *ctx, const BatchArgs &a, int b, const Bucket &bk)
+{
+    WarpLayout L = warp_layout(a.n, bk.max_ns, bk.max_r, bk.max_n);
+    size_t smem = (size_t)L.bytes * WARPS_PER_BLOCK;
+    MBE_CHECK(smem <= ctx->smem_optin, MBE_EUNSUPPORTED, "casci_batch: warp solver needs %zu B shared memory",
+              smem);
+    MBE_CU(cudaFuncSetAttribute(k_casci_warp<DPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_casci_warp<DPL>, WARPS_PER_BLOCK * 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    int grid = ctx->sm_count * per_sm;
+    TimedLaunch tl(ctx, a.order, 0, DPL);
+    k_casci_warp<DPL><<<grid, WARPS_PER_BLOCK * 32, smem, ctx->stream>>>(a, b, L);
+    MBE_CU(cudaGetLastError());
+    ++ctx->launches;
+    return tl.done();
+}
+
+static int block_grid(mbe_ctx *ctx, int n, int *grid, size_t *smem)
+{
+    BlockSmem S = block_smem(n);
+    *smem = (size_t)S.bytes;
+    MBE_CHECK(*smem <= ctx->smem_optin, MBE_EUNSUPPORTED, "casci_batch: block solver needs %zu B shared memory",
+              *smem);
+    MBE_CU(cudaFuncSetAttribute(k_casci_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem));
+    int per_sm = 0;
+    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_casci_block, CTA_THREADS, *smem));
+    if (per_sm < 1) per_sm = 1;
+    *grid = ctx->sm_count * per_sm;
+    return MBE_OK;
+}
+
+}  // namespace mbe
+
+using namespace mbe;
+
+extern "C" int casci_batch(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
+                           int n_ref, const int32_t *ref_orbs, double e_ref_corr, int order,
+                           int64_t n_tuples, const int32_t *tuples, const mbe_opts *opts, double *eps_out,
+                           int32_t *status_out, int32_t *iters_out)
+{
+    MBE_CHECK(ctx != nullptr && h1 != nullptr && eri != nullptr && occ != nullptr && eps_out != nullptr &&
+                  status_out != nullptr,
+              MBE_EINVAL, "casci_batch: NULL argument");
+    MBE_CHECK(norb >= 1 && norb <= MBE_MAX_NORB, MBE_EINVAL, "casci_batch: norb %d outside 1..%d", norb,
+              MBE_MAX_NORB);
+    MBE_CHECK(n_ref >= 0 && order >= 0 && n_tuples >= 0, MBE_EINVAL, "casci_batch: negative size");
+    MBE_CHECK(n_ref == 0 || ref_orbs != nullptr, MBE_EINVAL, "casci_batch: ref_orbs is NULL");
+    MBE_CHECK(order > 0 ? (tuples != nullptr || n_tuples == 0) : n_tuples <= 1, MBE_EINVAL,
+              "casci_batch: order 0 computes the reference space alone (n_tuples <= 1)");
+    const int n = n_ref + order;
+    MBE_CHECK(n >= 1, MBE_EINVAL, "casci_batch: empty active space");
+    MBE_CHECK(n <= MBE_MAX_CAS, MBE_EUNSUPPORTED, "casci_batch: |R| + order = %d > %d", n, MBE_MAX_CAS);
+    MBE_CHECK(n_tuples < (1LL << 31), MBE_EUNSUPPORTED, "casci_batch: n_tuples >= 2^31");
+    mbe_opts o;
+    if (opts) o = *opts; else mbe_default_opts(&o);
+    MBE_CHECK(o.precision == MBE_PREC_FP64 || o.precision == MBE_PREC_MIXED, MBE_EINVAL,
+              "casci_batch: unknown precision %d", o.precision);
+    MBE_CHECK(o.tol > 0 && o.tol_switch > 0 && o.max_iter >= 1 && o.fp64_final_iters >= 0, MBE_EINVAL,
+              "casci_batch: bad options");
+    if (n_tuples == 0) return MBE_OK;
+    MBE_CU(cudaSetDevice(ctx->device));
+
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    std::vector<int> ref(ref_orbs, ref_orbs + n_ref);
+    std::sort(ref.begin(), ref.end());
+    for (int i = 0; i < n_ref; ++i) {
+        MBE_CHECK(ref[i] >= 0 && ref[i] < norb && (i == 0 || ref[i] != ref[i - 1]), MBE_EINVAL,
+                  "casci_batch: reference orbital %d out of range or repeated", ref[i]);
+        a.ref[i] = ref[i];
+    }
+    a.norb = norb;
+    a.n = n;
+    a.n_ref = n_ref;
+    a.order = order;
+    a.eri = eri;
+    a.occ = occ;
+    a.tuples = order > 0 ? tuples : nullptr;
+    a.n_tuples = n_tuples;
+    a.e_ref_corr = e_ref_corr;
+    a.precision = o.precision;
+    a.tol = o.tol;
+    a.tol_switch = o.tol_switch;
+    a.max_iter = o.max_iter;
+    a.min_fp64 = o.fp64_final_iters;
+    a.eps = eps_out;
+    a.status = status_out;
+    a.iters = iters_out;
+
+    // Classes k = 0..n and their buckets.
+    ClassifyArgs cl;
+    std::vector<Bucket> buckets;
+    int warp_bucket_of_dpl[5] = {-1, -1, -1, -1, -1};
+    int block_bucket = -1;
+    int max_block_ns = 0;
+    for (int k = 0; k <= n; ++k) {
+        const StringTable *st = nullptr;
+        int rc = get_table(ctx, n, k, &st);
+        if (rc) return rc;
+        a.cls[k].strings = st->strings;
+        a.cls[k].table = st->table;
+        a.cls[k].ns = (int)st->ns;
+        a.cls[k].r = st->r;
+        int64_t N = st->ns * st->ns;
+        int b;
+        if (n <= WARP_MAX_N && N <= WARP_MAX_NDET) {
+            int di = 0;
+            while (DPL_SET[di] * 32 < N) ++di;
+            if (warp_bucket_of_dpl[di] < 0) {
+                warp_bucket_of_dpl[di] = (int)buckets.size();
+                buckets.push_back(Bucket{true, DPL_SET[di], 0, 0, 0});
+            }
+            b = warp_bucket_of_dpl[di];
+        } else {
+            if (block_bucket < 0) {
+                block_bucket = (int)buckets.size();
+                buckets.push_back(Bucket{false, 0, 0, 0, 0});
+            }
+            b = block_bucket;
+            max_block_ns = std::max(max_block_ns, (int)st->ns);
+        }
+        Bucket &bk = buckets[b];
+        bk.max_ns = std::max(bk.max_ns, (int)st->ns);
+        bk.max_r = std::max(bk.max_r, st->r);
+        bk.max_n = std::max(bk.max_n, (int)N);
+        cl.bucket_of_k[k] = b;
+    }
+    const int nb = (int)buckets.size();
+    cl.nbuckets = nb;
+
+    int block_grid_n = 0;
+    size_t block_smem_bytes = 0;
+    size_t slot_bytes = 0;
+    if (block_bucket >= 0) {
+        int rc = block_grid(ctx, n, &block_grid_n, &block_smem_bytes);
+        if (rc) return rc;
+        slot_bytes = slot_layout(max_block_ns, max_block_ns * max_block_ns).bytes;
+    }
+
+    size_t bytes = align256((size_t)norb * norb * 8) + align256((size_t)n_tuples * 4) * 2 +
+                   4 * align256((MAX_BUCKETS + 1) * 8) + (size_t)block_grid_n * slot_bytes + 1024;
+    void *ws = nullptr;
+    int rc = workspace(ctx, bytes, &ws);
+    if (rc) return rc;
+    Bump bump(ws);
+    double *F = bump.take<double>((size_t)norb * norb);
+    int32_t *key = bump.take<int32_t>(n_tuples);
+    int32_t *perm = bump.take<int32_t>(n_tuples);
+    int64_t *counts = bump.take<int64_t>(MAX_BUCKETS + 1);
+    unsigned long long *cursor = bump.take<unsigned long long>(MAX_BUCKETS + 1);
+    unsigned long long *counters = bump.take<unsigned long long>(MAX_BUCKETS + 1);
+    int64_t *bucket_off = bump.take<int64_t>(MAX_BUCKETS + 1);
+    char *scratch = nullptr;
+    if (block_grid_n > 0) scratch = bump.take<char>((size_t)block_grid_n * slot_bytes);
+
+    a.F = F;
+    a.perm = perm;
+    a.bucket_off = bucket_off;
+    a.counters = counters;
+    a.scratch = scratch;
+    a.slot_bytes = slot_bytes;
+
+    MBE_CU(cudaMemsetAsync(counts, 0, 3 * align256((MAX_BUCKETS + 1) * 8), ctx->stream));
+    k_core_fock<<<(norb * norb + 127) / 128, 128, 0, ctx->stream>>>(norb, h1, eri, occ, F);
+    unsigned g = (unsigned)((n_tuples + 255) / 256);
+    k_classify<<<g, 256, 0, ctx->stream>>>(a, cl, key, counts);
+    k_scatter<<<g, 256, 0, ctx->stream>>>(n_tuples, nb, key, counts, cursor, bucket_off, perm);
+    MBE_CU(cudaGetLastError());
+    ctx->launches += 3;
+    // Largest problems first, so that the long solves start early.
+    std::vector<int> order_b(nb);
+    for (int b = 0; b < nb; ++b) order_b[b] = b;
+    std::sort(order_b.begin(), order_b.end(),
+              [&](int x, int y) { return buckets[x].max_n > buckets[y].max_n; });
+    for (int b : order_b) {
+        const Bucket &bk = buckets[b];
+        if (!bk.warp) {
+            TimedLaunch tl(ctx, order, 1, 0);
+            k_casci_block<<<block_grid_n, CTA_THREADS, block_smem_bytes, ctx->stream>>>(a, b);
+            MBE_CU(cudaGetLastError());
+            ++ctx->launches;
+            rc = tl.done();
+            if (rc) return rc;
+            continue;
+        }
+        switch (bk.dpl) {
+            case 1: rc = launch_warp<1>(ctx, a, b, bk); break;
+            case 2: rc = launch_warp<2>(ctx, a, b, bk); break;
+            case 4: rc = launch_warp<4>(ctx, a, b, bk); break;
+            case 8: rc = launch_warp<8>(ctx, a, b, bk); break;
+            default: rc = launch_warp<13>(ctx, a, b, bk); break;
+        }
+        if (rc) return rc;
+    }
+    return MBE_OK;
+}
+
+// ------------------------------------------------------------------ single active space sigma
+
+namespace mbe {
+
+// One block: h_eff, V, h', Hs and the diagonal of the active space a.ref[0..n).
+__global__ void __launch_bounds__(CTA_THREADS)
+    k_sigma_setup(BatchArgs a, ClassInfo ci, double *V_out, double *Hs_out, double *diag_out)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int n = a.n, P = n * (n + 1) / 2;
+    const BlockSmem S = block_smem(n);
+    int *A = (int *)(smem + S.off_A);
+    if (threadIdx.x == 0) build_A(a, 0, A);
+    __syncthreads();
+    Problem pb;
+    pb.n = n;
+    pb.P = P;
+    pb.k = 0;
+    pb.Ns = ci.ns;
+    pb.N = ci.ns * ci.ns;
+    pb.R = ci.r;
+    pb.RS = ci.r;
+    pb.HSS = odd_stride(ci.ns);
+    pb.str = ci.strings;
+    pb.tab = ci.table;
+    pb.A = A;
+    pb.pp = (const short *)(smem + S.off_pp);
+    pb.h = (double *)(smem + S.off_h);
+    pb.hp = (double *)(smem + S.off_hp);
+    pb.V64 = (double *)(smem + S.off_V64);
+    pb.V32 = (float *)(smem + S.off_V32);
+    pb.Hs64 = Hs_out;
+    pb.Hs32 = nullptr;
+    pb.diag = diag_out;
+    pb.c = nullptr;
+    setup_problem<BlockGroup>(a, pb, false);
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) V_out[e] = pb.V64[e];
+}
+
+__global__ void __launch_bounds__(CTA_THREADS)
+    k_sigma_apply(int n, ClassInfo ci, const double *V, const double *Hs, const double *c, double *sigma)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int P = n * (n + 1) / 2;
+    double *Vs = (double *)smem;
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) Vs[e] = V[e];
+    __syncthreads();
+    Problem pb;
+    pb.n = n;
+    pb.P = P;
+    pb.Ns = ci.ns;
+    pb.N = ci.ns * ci.ns;
+    pb.R = ci.r;
+    pb.RS = ci.r;
+    pb.HSS = odd_stride(ci.ns);
+    pb.tab = ci.table;
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < pb.N; d += (int64_t)gridDim.x * blockDim.x)
+        sigma[d] = sigma_elem<double>(pb, Vs, Hs, c, (int)d);
+}
+
+}  // namespace mbe
+
+extern "C" int casci_sigma(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
+                           int n_cas, const int32_t *cas_orbs, const double *c, double *sigma, double *diag)
+{
+    MBE_CHECK(ctx && h1 && eri && occ && cas_orbs && c && sigma, MBE_EINVAL, "casci_sigma: NULL argument");
+    MBE_CHECK(norb >= 1 && norb <= MBE_MAX_NORB, MBE_EINVAL, "casci_sigma: norb %d", norb);
+    MBE_CHECK(n_cas >= 1 && n_cas <= norb, MBE_EINVAL, "casci_sigma: n_cas %d", n_cas);
+    MBE_CHECK(n_cas <= MBE_MAX_CAS, MBE_EUNSUPPORTED, "casci_sigma: n_cas %d > %d", n_cas, MBE_MAX_CAS);
+    MBE_CU(cudaSetDevice(ctx->device));
+    std::vector<int> A(cas_orbs, cas_orbs + n_cas);
+    std::sort(A.begin(), A.end());
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int i = 0; i < n_cas; ++i) {
+        MBE_CHECK(A[i] >= 0 && A[i] < norb && (i == 0 || A[i] != A[i - 1]), MBE_EINVAL,
+                  "casci_sigma: active orbital %d out of range or repeated", A[i]);
+        a.ref[i] = A[i];
+    }
+    // The electron count needs occ on the host: one small synchronous copy.
+    std::vector<uint8_t> occ_h(norb);
+    MBE_CU(cudaMemcpyAsync(occ_h.data(), occ, norb, cudaMemcpyDeviceToHost, ctx->stream));
+    MBE_CU(cudaStreamSynchronize(ctx->stream));
+    int k = 0;
+    for (int i = 0; i < n_cas; ++i) k += occ_h[A[i]] ? 1 : 0;
+    const StringTable *st = nullptr;
+    int rc = get_table(ctx, n_cas, k, &st);
+    if (rc) return rc;
+    ClassInfo ci{st->strings, st->table, (int)st->ns, st->r};
+    const int P = n_cas * (n_cas + 1) / 2;
+    const int64_t N = st->ns * st->ns;
+    size_t hs_elems = (size_t)st->ns * odd_stride((int)st->ns);
+    size_t bytes = align256((size_t)norb * norb * 8) + align256((size_t)P * P * 8) + align256(hs_elems * 8) +
+                   align256((size_t)N * 8) + 1024;
+    void *ws = nullptr;
+    rc = workspace(ctx, bytes, &ws);
+    if (rc) return rc;
+    Bump bump(ws);
+    double *F = bump.take<double>((size_t)norb * norb);
+    double *V = bump.take<double>((size_t)P * P);
+    double *Hs = bump.take<double>(hs_elems);
+    double *dg = diag ? diag : bump.take<double>((size_t)N);
+    a.norb = norb;
+    a.n = n_cas;
+    a.n_ref = n_cas;
+    a.order = 0;
+    a.eri = eri;
+    a.occ = occ;
+    a.F = F;
+    a.n_tuples = 1;
+    k_core_fock<<<(norb * norb + 127) / 128, 128, 0, ctx->stream>>>(norb, h1, eri, occ, F);
+    BlockSmem S = block_smem(n_cas);
+    MBE_CU(cudaFuncSetAttribute(k_sigma_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, S.bytes));
+    k_sigma_setup<<<1, CTA_THREADS, S.bytes, ctx->stream>>>(a, ci, V, Hs, dg);
+    size_t smem = (size_t)P * P * 8;
+    MBE_CU(cudaFuncSetAttribute(k_sigma_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int64_t blocks = (N + CTA_THREADS - 1) / CTA_THREADS;
+    int grid = (int)std::min<int64_t>(blocks, (int64_t)ctx->sm_count * 8);
+    k_sigma_apply<<<grid, CTA_THREADS, smem, ctx->stream>>>(n_cas, ci, V, Hs, c, sigma);
+    MBE_CU(cudaGetLastError());
+    ctx->launches += 3;
+    return MBE_OK;
+}

@@ -1,0 +1,133 @@
+// Internal declarations shared by the translation units of the MBE-FCI engine.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstddef>
+#include <vector>
+
+#include "mbe.h"
+
+namespace mbe {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define MBE_CU(call)                                                     \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return ::mbe::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define MBE_CHECK(cond, code, ...)              \
+    do {                                        \
+        if (!(cond)) {                          \
+            ::mbe::set_error(__VA_ARGS__);      \
+            return (code);                      \
+        }                                       \
+    } while (0)
+
+// ------------------------------------------------------------------ combinatorics
+
+__host__ __device__ inline int64_t binom(int n, int k)
+{
+    if (k < 0 || n < 0 || k > n) return 0;
+    if (k > n - k) k = n - k;
+    int64_t c = 1;
+    for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
+    return c;
+}
+
+// Packed index of the unordered orbital pair {p, q}.
+__host__ __device__ inline int pair_index(int p, int q)
+{
+    int hi = p > q ? p : q, lo = p > q ? q : p;
+    return hi * (hi + 1) / 2 + lo;
+}
+
+// Rank of a string (bit pattern) in ascending order among strings with the same
+// number of set bits: sum over set bits c_1 < c_2 < ... of C(c_i, i).
+__host__ __device__ inline int32_t string_rank(uint32_t s)
+{
+    int32_t r = 0;
+    int i = 0;
+    while (s) {
+#ifdef __CUDA_ARCH__
+        int c = __ffs((int)s) - 1;
+#else
+        int c = __builtin_ctz(s);
+#endif
+        ++i;
+        r += (int32_t)binom(c, i);
+        s &= s - 1;
+    }
+    return r;
+}
+
+// ------------------------------------------------------------------ string tables
+
+struct StringTable {
+    int n = 0, k = 0;
+    int64_t ns = 0;   // number of strings C(n, k)
+    int r = 0;        // replacement entries per string k (n - k + 1)
+    uint32_t *strings = nullptr;  // device [ns]
+    int32_t *table = nullptr;     // device [ns * r]
+};
+
+// Table entry packing: (J << 9) | (pair << 1) | negative
+__host__ __device__ inline int entry_J(int32_t e) { return e >> 9; }
+__host__ __device__ inline int entry_pair(int32_t e) { return (e >> 1) & 255; }
+__host__ __device__ inline int entry_neg(int32_t e) { return e & 1; }
+
+}  // namespace mbe
+
+// ------------------------------------------------------------------ context
+
+struct mbe_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    void *ws = nullptr;
+    size_t ws_size = 0;
+    mbe::StringTable tables[MBE_MAX_STRING_ORB + 1][MBE_MAX_STRING_ORB + 1];
+    int64_t launches = 0;  // kernels launched by this context
+    bool timing = false;
+    struct Pending {
+        mbe_timing rec;
+        cudaEvent_t start, stop;
+    };
+    std::vector<Pending> pending;
+};
+
+namespace mbe {
+
+// Device workspace of at least `bytes` (stream-ordered growth).  The returned
+// pointer stays valid until the next call that grows the workspace.
+int workspace(mbe_ctx *ctx, size_t bytes, void **out);
+
+// Cached device string table of class (n, k); builds it on first use.
+int get_table(mbe_ctx *ctx, int n, int k, const StringTable **out);
+
+// Bump allocator over a workspace region.
+struct Bump {
+    char *base;
+    size_t off = 0;
+    explicit Bump(void *b) : base((char *)b) {}
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = (T *)(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace mbe

@@ -1,0 +1,185 @@
+// a8: increment recursion (Eq. 2); a9: order sums and total (Eq. 1 / Eq. 3);
+// the reference-determinant energy.
+#include "common.cuh"
+
+namespace mbe {
+
+struct LowerLists {
+    const int32_t *tuples[MBE_MAX_ORDER];
+    const double *incs[MBE_MAX_ORDER];
+    int64_t count[MBE_MAX_ORDER];
+};
+
+// Position of the m-tuple `key` in a lexicographically sorted list, or -1.
+__device__ inline int64_t find_tuple(const int32_t *list, int64_t len, int m, const int32_t *key)
+{
+    int64_t lo = 0, hi = len - 1;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) >> 1;
+        const int32_t *row = list + mid * m;
+        int cmp = 0;
+        for (int i = 0; i < m; ++i) {
+            if (row[i] != key[i]) {
+                cmp = row[i] < key[i] ? -1 : 1;
+                break;
+            }
+        }
+        if (cmp == 0) return mid;
+        if (cmp < 0) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+// One thread per tuple: Delta eps = eps - sum over the proper subsets (bit masks
+// 1 .. 2^order - 2 of the tuple's positions, in that order) of their increments.
+__global__ void k_increments(int order, int64_t n_tuples, const int32_t *tuples, const double *eps,
+                             LowerLists L, double *inc_out)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tuples) return;
+    int32_t tup[MBE_MAX_ORDER], sub[MBE_MAX_ORDER];
+    for (int i = 0; i < order; ++i) tup[i] = tuples[t * order + i];
+    double s = 0.0;
+    const unsigned full = (1u << order) - 1u;
+    for (unsigned mask = 1; mask < full; ++mask) {
+        int m = 0;
+        for (int i = 0; i < order; ++i)
+            if (mask & (1u << i)) sub[m++] = tup[i];
+        int64_t pos = find_tuple(L.tuples[m - 1], L.count[m - 1], m, sub);
+        if (pos >= 0) s += L.incs[m - 1][pos];
+    }
+    inc_out[t] = eps[t] - s;
+}
+
+// Fixed-shape reduction: block m sums list m (strided partial sums, then a tree).
+constexpr int RED_THREADS = 1024;
+
+struct SumLists {
+    const double *incs[MBE_MAX_ORDER];
+    int64_t count[MBE_MAX_ORDER];
+};
+
+__global__ void __launch_bounds__(RED_THREADS) k_order_sums(SumLists S, double *e_order_out)
+{
+    __shared__ double part[RED_THREADS];
+    const int m = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < S.count[m]; i += RED_THREADS) s += S.incs[m][i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) e_order_out[m] = part[0];
+}
+
+__global__ void k_total(int n_orders, const double *e_order, const double *e_phi, double e_ref_corr,
+                        double *e_total)
+{
+    double s = (e_phi ? e_phi[0] : 0.0) + e_ref_corr;
+    for (int m = 0; m < n_orders; ++m) s += e_order[m];
+    e_total[0] = s;
+}
+
+// E_Phi = sum_{i in O} 2 h_ii + sum_{i,j in O} [2 (ii|jj) - (ij|ji)]
+__global__ void k_phi_energy(int norb, const double *h1, const double *eri, const uint8_t *occ, double *out)
+{
+    __shared__ double part[256];
+    double s = 0.0;
+    for (int e = threadIdx.x; e < norb * norb; e += blockDim.x) {
+        int i = e / norb, j = e - i * norb;
+        if (!occ[i] || !occ[j]) continue;
+        size_t iijj = (((size_t)i * norb + i) * norb + j) * norb + j;
+        size_t ijji = (((size_t)i * norb + j) * norb + j) * norb + i;
+        s += 2.0 * eri[iijj] - eri[ijji];
+        if (i == j) s += 2.0 * h1[i * norb + i];
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = part[0];
+}
+
+}  // namespace mbe
+
+using namespace mbe;
+
+extern "C" {
+
+int mbe_phi_energy(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
+                   double *e_phi)
+{
+    MBE_CHECK(ctx && h1 && eri && occ && e_phi, MBE_EINVAL, "mbe_phi_energy: NULL argument");
+    MBE_CHECK(norb >= 1 && norb <= MBE_MAX_NORB, MBE_EINVAL, "mbe_phi_energy: norb %d", norb);
+    MBE_CU(cudaSetDevice(ctx->device));
+    k_phi_energy<<<1, 256, 0, ctx->stream>>>(norb, h1, eri, occ, e_phi);
+    MBE_CU(cudaGetLastError());
+    ++ctx->launches;
+    return MBE_OK;
+}
+
+int mbe_increments(mbe_ctx *ctx, int order, int64_t n_tuples, const int32_t *tuples, const double *eps,
+                   int n_lower, const int64_t *n_lower_tuples, const int32_t *const *lower_tuples,
+                   const double *const *lower_incs, double *inc_out)
+{
+    MBE_CHECK(ctx != nullptr, MBE_EINVAL, "mbe_increments: ctx is NULL");
+    MBE_CHECK(order >= 1 && order <= MBE_MAX_ORDER && order <= 31, MBE_EINVAL,
+              "mbe_increments: order %d outside 1..%d", order, MBE_MAX_ORDER);
+    MBE_CHECK(n_lower == order - 1, MBE_EINVAL, "mbe_increments: n_lower (%d) must be order - 1 (%d)", n_lower,
+              order - 1);
+    MBE_CHECK(n_tuples >= 0, MBE_EINVAL, "mbe_increments: n_tuples < 0");
+    if (n_tuples == 0) return MBE_OK;
+    MBE_CHECK(tuples && eps && inc_out, MBE_EINVAL, "mbe_increments: NULL argument");
+    LowerLists L;
+    for (int m = 0; m < MBE_MAX_ORDER; ++m) {
+        L.tuples[m] = nullptr;
+        L.incs[m] = nullptr;
+        L.count[m] = 0;
+    }
+    for (int m = 0; m < n_lower; ++m) {
+        MBE_CHECK(n_lower_tuples && n_lower_tuples[m] >= 0, MBE_EINVAL, "mbe_increments: bad lower count");
+        L.count[m] = n_lower_tuples[m];
+        if (L.count[m] > 0) {
+            MBE_CHECK(lower_tuples && lower_incs && lower_tuples[m] && lower_incs[m], MBE_EINVAL,
+                      "mbe_increments: NULL lower list of order %d", m + 1);
+            L.tuples[m] = lower_tuples[m];
+            L.incs[m] = lower_incs[m];
+        }
+    }
+    MBE_CU(cudaSetDevice(ctx->device));
+    unsigned g = (unsigned)((n_tuples + 127) / 128);
+    k_increments<<<g, 128, 0, ctx->stream>>>(order, n_tuples, tuples, eps, L, inc_out);
+    MBE_CU(cudaGetLastError());
+    ++ctx->launches;
+    return MBE_OK;
+}
+
+int mbe_total(mbe_ctx *ctx, int n_orders, const int64_t *n_tuples, const double *const *incs,
+              const double *e_phi, double e_ref_corr, double *e_order_out, double *e_total_out)
+{
+    MBE_CHECK(ctx && e_order_out && e_total_out, MBE_EINVAL, "mbe_total: NULL argument");
+    MBE_CHECK(n_orders >= 0 && n_orders <= MBE_MAX_ORDER, MBE_EINVAL, "mbe_total: n_orders %d", n_orders);
+    SumLists S;
+    for (int m = 0; m < MBE_MAX_ORDER; ++m) {
+        S.incs[m] = nullptr;
+        S.count[m] = 0;
+    }
+    for (int m = 0; m < n_orders; ++m) {
+        MBE_CHECK(n_tuples && incs && n_tuples[m] >= 0 && (n_tuples[m] == 0 || incs[m]), MBE_EINVAL,
+                  "mbe_total: bad list %d", m);
+        S.incs[m] = incs[m];
+        S.count[m] = n_tuples[m];
+    }
+    MBE_CU(cudaSetDevice(ctx->device));
+    if (n_orders > 0) k_order_sums<<<n_orders, RED_THREADS, 0, ctx->stream>>>(S, e_order_out);
+    k_total<<<1, 1, 0, ctx->stream>>>(n_orders, e_order_out, e_phi, e_ref_corr, e_total_out);
+    MBE_CU(cudaGetLastError());
+    ctx->launches += (n_orders > 0 ? 2 : 1);
+    return MBE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+"""CPU-side checks of the C-ABI library: it builds for sm_103a, loads, and exports
+every entry point that include/mbe.h declares.  No compute call (no GPU here)."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mbe.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:int|void|const char \*)\s*\**\s*(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1910_03527_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for want in ("mbe_tuples", "casci_batch", "mbe_increments", "mbe_total", "mbe_string_table",
+                 "casci_sigma", "mbe_phi_energy", "mbe_ctx_create", "mbe_ctx_destroy"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_matches_header(libpath):
+    L = ctypes.CDLL(libpath)
+    for n in declared_functions():
+        assert hasattr(L, n)
+    from paper_1910_03527_gb300 import EXPORTS
+    assert sorted(EXPORTS) == declared_functions()
+
+
+def test_default_opts_without_gpu(libpath):
+    from paper_1910_03527_gb300.binding import MbeOpts, lib
+    o = MbeOpts()
+    lib().mbe_default_opts(ctypes.byref(o))
+    assert o.precision == 0 and o.tol == 1e-6 and o.max_iter == 200 and o.fp64_final_iters == 2
+
+
+def test_count_query_needs_no_gpu(libpath):
+    # The count-only form of mbe_tuples is host arithmetic and launches nothing.
+    from paper_1910_03527_gb300.binding import lib, _i32_host, _u8_host
+    n = ctypes.c_int64()
+    occ = [1] * 11 + [0] * 11
+    rc = lib().mbe_tuples(None, 22, _u8_host(occ), 22, _i32_host(range(22)), 0, _i32_host([]), 6, 1,
+                          ctypes.byref(n), None)
+    assert rc == 0 and n.value == 73689
+
+
+def test_product_path_refuses_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1910_03527_gb300 import Context, MbeError
+    with pytest.raises(MbeError):
+        Context(0)
+
+
+def test_oracle_is_not_imported_by_the_package():
+    pkg = os.path.join(ROOT, "paper_1910_03527_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in text.replace("no CPU", ""), f
