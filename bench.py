@@ -280,7 +280,8 @@ def run_ours(args):
     value_64 = ws * n_tuples / (ms_step_64 / 1e3)
 
     # accuracy of the mixed form against float64 on the same tuples
-    diff = max(float((a - b).abs().max().item()) for a, b in zip(out_mix["eps"], out_64["eps"]))
+    diff = max([float((a - b).abs().max().item()) for a, b in zip(out_mix["eps"], out_64["eps"])
+                if a.numel() > 0] + [0.0])
     bad = sum(int((s != 0).sum().item()) for s in out_mix["status"] + out_64["status"])
 
     # ---- roofline of the dominant solver kernel (per launch, CUDA events inside the library)
@@ -399,6 +400,29 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_ncu_case(args):
+    """A small, fixed case for ncu captures: the order-`args.ncu_order` tuples of the
+    workload through casci_batch, `args.steps` times, in the given precision."""
+    import torch
+
+    import paper_1910_03527_gb300 as eng
+    from workloads import workload
+
+    eng.build()
+    w = workload(WORKLOAD)
+    dev = torch.device("cuda", 0)
+    ctx = eng.Context(0)
+    h1, eri, occ = (torch.tensor(x, device=dev) for x in (w.h1, w.eri, w.occ))
+    tup = ctx.mbe_tuples(w.norb, w.occ.tolist(), w.exp, w.ref, args.ncu_order, w.skip)
+    opts = eng.Opts(precision=args.ncu_case)
+    for _ in range(max(args.steps, 1)):
+        eps, st, it = ctx.casci_batch(h1, eri, occ, w.ref, 0.0, args.ncu_order, tup, opts)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.ncu_case, "order": args.ncu_order, "tuples": int(tup.shape[0]),
+                      "non_ok": int((st != 0).sum().item())}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,9 +433,15 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--ncu-case", choices=["fp64", "mixed"], default=None,
+                    help="run only casci_batch on one order of the workload (for ncu captures)")
+    ap.add_argument("--ncu-order", type=int, default=6)
     args = ap.parse_args()
     if args.oracle_sample is not None:
         print(json.dumps(oracle_sample(args.oracle_sample)))
+        return
+    if args.ncu_case is not None:
+        run_ncu_case(args)
         return
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -118,7 +118,7 @@ class Opts:
     precision: str = "fp64"  # "fp64" or "mixed"
     tol: float = 1e-6
     tol_switch: float = 1e-4
-    max_iter: int = 200
+    max_iter: int = 500
     fp64_final_iters: int = 2
 
     def to_c(self) -> MbeOpts:

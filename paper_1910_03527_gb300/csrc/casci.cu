@@ -387,7 +387,7 @@ __device__ inline double guess_noise(int d)
     return (double)(h & 0xffffu) / 32768.0 - 1.0;
 }
 
-constexpr double GUESS_NOISE = 1e-2;
+constexpr double GUESS_NOISE = 1e-4;
 
 struct PhaseOut {
     double lambda, rnorm;
@@ -735,9 +735,13 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
 
 // ------------------------------------------------------------------ block solver
 
-// Per-block workspace slot: vectors and Hs in global memory.
+constexpr int MMAX = 12;  // Davidson subspace of the block solver
+constexpr int KRED = 16;  // values per block reduction (>= MMAX + 1)
+
+// Per-block workspace slot: the Davidson basis V, its image W = H V, the Ritz
+// vector x and H x, a spare correction vector, the diagonal and Hs.
 struct SlotLayout {
-    size_t off_x, off_hx, off_p, off_hp, off_t, off_ht, off_diag, off_Hs64, off_Hs32, bytes;
+    size_t off_V, off_W, off_x, off_hx, off_t, off_diag, off_Hs64, off_Hs32, vec, bytes;
 };
 
 __host__ __device__ inline SlotLayout slot_layout(int ns, int N)
@@ -746,12 +750,12 @@ __host__ __device__ inline SlotLayout slot_layout(int ns, int N)
     size_t o = 0;
     size_t vec = ((size_t)N * 8 + 255) & ~(size_t)255;
     int HSS = odd_stride(ns);
+    L.vec = vec;
+    L.off_V = o; o += vec * MMAX;
+    L.off_W = o; o += vec * MMAX;
     L.off_x = o; o += vec;
     L.off_hx = o; o += vec;
-    L.off_p = o; o += vec;
-    L.off_hp = o; o += vec;
     L.off_t = o; o += vec;
-    L.off_ht = o; o += vec;
     L.off_diag = o; o += vec;
     L.off_Hs64 = o; o += ((size_t)ns * HSS * 8 + 255) & ~(size_t)255;
     L.off_Hs32 = o; o += ((size_t)ns * HSS * 4 + 255) & ~(size_t)255;
@@ -760,7 +764,8 @@ __host__ __device__ inline SlotLayout slot_layout(int ns, int N)
 }
 
 struct BlockSmem {  // dynamic shared memory of the block solver
-    int off_A, off_pp, off_h, off_hp, off_V64, off_V32, off_red, bytes;
+    int off_A, off_pp, off_h, off_hp, off_V64, off_V32, off_red, off_G, off_A32, off_E32, off_ev, off_y,
+        off_yp, off_r, off_misc, bytes;
 };
 
 __host__ __device__ inline BlockSmem block_smem(int n)
@@ -773,58 +778,229 @@ __host__ __device__ inline BlockSmem block_smem(int n)
     S.off_hp = o; o = al16(o + 8 * P);
     S.off_V64 = o; o = al16(o + 8 * P * P);
     S.off_V32 = o; o = al16(o + 4 * P * P);
-    S.off_red = o; o = al16(o + 8 * 32 * 8);
+    S.off_red = o; o = al16(o + 8 * 32 * KRED);
+    S.off_G = o; o = al16(o + 8 * MMAX * MMAX);
+    S.off_A32 = o; o = al16(o + 4 * MMAX * MMAX);
+    S.off_E32 = o; o = al16(o + 4 * MMAX * MMAX);
+    S.off_ev = o; o = al16(o + 4 * MMAX);
+    S.off_y = o; o = al16(o + 8 * MMAX);
+    S.off_yp = o; o = al16(o + 8 * MMAX);
+    S.off_r = o; o = al16(o + 8 * MMAX);
+    S.off_misc = o; o = al16(o + 8 * 4);
     S.bytes = o;
     return S;
 }
 
+// Sums of the first k of the values v[0..KRED) over the block; every thread gets
+// the totals.  red: >= 32 * KRED elements of T.
 template <typename T>
-__device__ PhaseOut davidson_block(const Problem &pb, T *x, T *hx, T *p, T *hp, T *t, T *ht, double *red,
-                                   double tol, int min_iter, int max_iter, bool steer)
+__device__ inline void block_sum_n(T (&v)[KRED], int k, T *red)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < KRED; ++i)
+        if (i < k) v[i] = warp_sum(v[i]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < KRED; ++i)
+            if (i < k) red[w * KRED + i] = v[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < KRED; ++i)
+        if (i < k) {
+            T s = 0;
+            for (int j = 0; j < nw; ++j) s += red[j * KRED + i];
+            v[i] = s;
+        }
+    __syncthreads();
+}
+
+// Lowest eigenpair of the m x m symmetric Rayleigh matrix G (shared memory,
+// float64, row stride MMAX), computed by one warp: a float32 cyclic Jacobi on
+// G - G00 I gives all eigenpairs; in the float64 phase two Newton steps in that
+// eigenbasis,  z = y - sum_{k != 0} e_k (e_k . r) / (theta_k - theta),
+// r = G y - theta y,  theta = y.G y, make the lowest pair float64-accurate.
+// Output: y[0..m) (shared, float64, unit norm) and misc[0] = theta.
+template <bool REFINE>
+__device__ void small_eig_warp(const double *G, int m, float *A, float *E, float *ev, double *y, double *r,
+                               double *misc)
+{
+    const int lane = threadIdx.x & 31;
+    const double shift = G[0];
+    for (int e = lane; e < m * m; e += 32) {
+        int i = e / m, j = e - i * m;
+        A[i * MMAX + j] = (float)(G[i * MMAX + j] - (i == j ? shift : 0.0));
+        E[i * MMAX + j] = (i == j) ? 1.0f : 0.0f;
+    }
+    __syncwarp();
+    for (int sweep = 0; sweep < 10; ++sweep) {
+        float off = 0.0f, dia = 0.0f;
+        if (lane < m)
+            for (int j = 0; j < m; ++j) {
+                float v = A[lane * MMAX + j];
+                if (j == lane) dia += v * v; else off += v * v;
+            }
+        off = warp_sum(off);
+        dia = warp_sum(dia);
+        if (off <= 1e-14f * dia || off < 1e-36f) break;
+        for (int p = 0; p < m - 1; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                float apq = A[p * MMAX + q];
+                if (fabsf(apq) < 1e-36f) continue;
+                float app = A[p * MMAX + p], aqq = A[q * MMAX + q];
+                float th = (aqq - app) / (2.0f * apq);
+                float t = 1.0f / (fabsf(th) + sqrtf(th * th + 1.0f));
+                if (th < 0.0f) t = -t;
+                float c = rsqrtf(t * t + 1.0f), s = t * c;
+                float ajp = 0.f, ajq = 0.f, ejp = 0.f, ejq = 0.f;
+                if (lane < m) {
+                    ajp = A[lane * MMAX + p];
+                    ajq = A[lane * MMAX + q];
+                    ejp = E[lane * MMAX + p];
+                    ejq = E[lane * MMAX + q];
+                }
+                __syncwarp();
+                if (lane < m) {
+                    if (lane != p && lane != q) {
+                        float np_ = c * ajp - s * ajq, nq = s * ajp + c * ajq;
+                        A[lane * MMAX + p] = np_;
+                        A[p * MMAX + lane] = np_;
+                        A[lane * MMAX + q] = nq;
+                        A[q * MMAX + lane] = nq;
+                    } else if (lane == p) {
+                        A[p * MMAX + p] = app - t * apq;
+                        A[p * MMAX + q] = 0.0f;
+                        A[q * MMAX + p] = 0.0f;
+                    } else {
+                        A[q * MMAX + q] = aqq + t * apq;
+                    }
+                    E[lane * MMAX + p] = c * ejp - s * ejq;
+                    E[lane * MMAX + q] = s * ejp + c * ejq;
+                }
+                __syncwarp();
+            }
+    }
+    float best = (lane < m) ? A[lane * MMAX + lane] : 3.0e38f;
+    int bi = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float ov = __shfl_xor_sync(FULL, best, o);
+        int oi = __shfl_xor_sync(FULL, bi, o);
+        if (ov < best || (ov == best && oi < bi)) {
+            best = ov;
+            bi = oi;
+        }
+    }
+    if (lane < m) {
+        ev[lane] = A[lane * MMAX + lane];
+        y[lane] = (double)E[lane * MMAX + bi];
+    }
+    __syncwarp();
+    double theta = shift + (double)best;
+    if (REFINE) {
+        for (int step = 0; step < 2; ++step) {
+            double g = 0.0, yi = (lane < m) ? y[lane] : 0.0;
+            if (lane < m)
+                for (int j = 0; j < m; ++j) g += G[lane * MMAX + j] * y[j];
+            double yy = warp_sum(yi * yi), ygy = warp_sum(yi * g);
+            theta = ygy / yy;
+            if (lane < m) r[lane] = g - theta * yi;
+            __syncwarp();
+            // coefficient of eigenvector k (lane k)
+            double ck = 0.0;
+            if (lane < m && lane != bi) {
+                for (int i = 0; i < m; ++i) ck += (double)E[i * MMAX + lane] * r[i];
+                double den = shift + (double)ev[lane] - theta;
+                ck = (fabs(den) > 1e-300) ? ck / den : 0.0;
+            }
+            __syncwarp();
+            if (lane < m) r[lane] = ck;  // reuse r for the coefficients
+            __syncwarp();
+            double z = yi;
+            if (lane < m)
+                for (int k = 0; k < m; ++k) z -= (double)E[lane * MMAX + k] * r[k];
+            double zz = warp_sum(z * z);
+            if (lane < m) y[lane] = z / sqrt(zz);
+            __syncwarp();
+        }
+        double g = 0.0, yi = (lane < m) ? y[lane] : 0.0;
+        if (lane < m)
+            for (int j = 0; j < m; ++j) g += G[lane * MMAX + j] * y[j];
+        theta = warp_sum(yi * g);
+    }
+    if (lane == 0) misc[0] = theta;
+    __syncwarp();
+}
+
+// One Davidson phase in precision T (block solver).  x: start vector in, Ritz
+// vector out.  V, W: MMAX vectors each, leading dimension ld (elements).
+template <typename T>
+__device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *x, T *hx, T *tx, char *smem,
+                                   const BlockSmem &S, double tol, int min_iter, int max_iter, bool steer)
 {
     const int tid = threadIdx.x, nt = blockDim.x, N = pb.N;
-    const T *V = sizeof(T) == 8 ? (const T *)pb.V64 : (const T *)pb.V32;
+    const T *Vi = sizeof(T) == 8 ? (const T *)pb.V64 : (const T *)pb.V32;
     const T *Hs = sizeof(T) == 8 ? (const T *)pb.Hs64 : (const T *)pb.Hs32;
-    T *tred = (T *)red;
+    T *red = (T *)(smem + S.off_red);
+    double *G = (double *)(smem + S.off_G);
+    float *A32 = (float *)(smem + S.off_A32);
+    float *E32 = (float *)(smem + S.off_E32);
+    float *ev = (float *)(smem + S.off_ev);
+    double *ys = (double *)(smem + S.off_y);
+    double *yps = (double *)(smem + S.off_yp);
+    double *rs = (double *)(smem + S.off_r);
+    double *misc = (double *)(smem + S.off_misc);
     PhaseOut o;
     o.nsig = 0;
     o.status = MBE_STATUS_OK;
+    T v[KRED];
     {
-        T v[1] = {0};
+        v[0] = 0;
         for (int d = tid; d < N; d += nt) v[0] += x[d] * x[d];
-        block_sum<T, 1>(v, tred);
+        block_sum_n<T>(v, 1, red);
         T inv = (T)1 / sqrt(v[0]);
-        for (int d = tid; d < N; d += nt) {
-            x[d] *= inv;
-            p[d] = 0;
-            hp[d] = 0;
-        }
+        for (int d = tid; d < N; d += nt) V[d] = x[d] * inv;
     }
     __syncthreads();
-    for (int d = tid; d < N; d += nt) hx[d] = sigma_elem<T>(pb, V, Hs, x, d);
+    for (int d = tid; d < N; d += nt) W[d] = sigma_elem<T>(pb, Vi, Hs, V, d);
     ++o.nsig;
-    T lam;
-    {
-        T v[1] = {0};
-        for (int d = tid; d < N; d += nt) v[0] += x[d] * hx[d];
-        block_sum<T, 1>(v, tred);
-        lam = v[0];
-    }
-    bool have_p = false;
-    T best = (T)3e38, rn = 0;
+    v[0] = 0;
+    for (int d = tid; d < N; d += nt) v[0] += V[d] * W[d];
+    block_sum_n<T>(v, 1, red);
+    if (tid == 0) G[0] = (double)v[0];
+    __syncthreads();
+    int m = 1;
+    bool have_prev = false;
+    double theta = 0.0;
+    T rn = 0;
+    T best = (T)3e38;
     int stall = 0;
     for (int it = 0;; ++it) {
-        T v1[1] = {0};
+        if (tid < 32) small_eig_warp<sizeof(T) == 8>(G, m, A32, E32, ev, ys, rs, misc);
+        __syncthreads();
+        theta = misc[0];
+        const T th = (T)theta;
+        T *tdst = (m < MMAX) ? V + (size_t)m * ld : tx;
+        v[0] = 0;
         for (int d = tid; d < N; d += nt) {
-            T r = hx[d] - lam * x[d];
-            v1[0] += r * r;
-            T den = (T)pb.diag[d] - lam;
+            T xs = 0, hs = 0;
+            for (int i = 0; i < m; ++i) {
+                T yi = (T)ys[i];
+                xs += yi * V[(size_t)i * ld + d];
+                hs += yi * W[(size_t)i * ld + d];
+            }
+            x[d] = xs;
+            hx[d] = hs;
+            T r = hs - th * xs;
+            v[0] += r * r;
+            T den = (T)pb.diag[d] - th;
             if (fabs(den) < (T)1e-4) den = den >= (T)0 ? (T)1e-4 : (T)-1e-4;
-            t[d] = r / den;
+            tdst[d] = r / den;
         }
-        block_sum<T, 1>(v1, tred);
-        rn = sqrt(v1[0]);
-        if (!isfinite(rn) || !isfinite(lam)) {
+        block_sum_n<T>(v, 1, red);
+        rn = sqrt(v[0]);
+        if (!isfinite(rn) || !isfinite(theta)) {
             o.status = MBE_STATUS_NONFINITE;
             break;
         }
@@ -841,84 +1017,125 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *x, T *hx, T *p, T *hp, 
                 break;
             }
         }
-        for (int pass = 0; pass < 2; ++pass) {
-            T v2[2] = {0, 0};
+        if (m == MMAX) {
+            // Thick restart: basis {x, previous Ritz vector}, orthonormalised twice.
             for (int d = tid; d < N; d += nt) {
-                v2[0] += x[d] * t[d];
-                v2[1] += p[d] * t[d];
+                T xp = 0, hxp = 0;
+                if (have_prev) {
+                    for (int i = 0; i < MMAX; ++i) {
+                        T yi = (T)yps[i];
+                        xp += yi * V[(size_t)i * ld + d];
+                        hxp += yi * W[(size_t)i * ld + d];
+                    }
+                }
+                V[d] = x[d];
+                W[d] = hx[d];
+                V[ld + d] = xp;
+                W[ld + d] = hxp;
             }
-            block_sum<T, 2>(v2, tred);
-            for (int d = tid; d < N; d += nt) t[d] -= v2[0] * x[d] + v2[1] * p[d];
+            __syncthreads();
+            int mnew = 1;
+            if (have_prev) {
+                for (int pass = 0; pass < 2; ++pass) {
+                    v[0] = 0;
+                    for (int d = tid; d < N; d += nt) v[0] += V[d] * V[ld + d];
+                    block_sum_n<T>(v, 1, red);
+                    for (int d = tid; d < N; d += nt) {
+                        V[ld + d] -= v[0] * V[d];
+                        W[ld + d] -= v[0] * W[d];
+                    }
+                }
+                v[0] = 0;
+                for (int d = tid; d < N; d += nt) v[0] += V[ld + d] * V[ld + d];
+                block_sum_n<T>(v, 1, red);
+                T nn = sqrt(v[0]);
+                if (nn > tiny_norm<T>()) {
+                    T inv = (T)1 / nn;
+                    for (int d = tid; d < N; d += nt) {
+                        V[ld + d] *= inv;
+                        W[ld + d] *= inv;
+                    }
+                    mnew = 2;
+                }
+            }
+            v[0] = v[1] = v[2] = 0;
+            for (int d = tid; d < N; d += nt) {
+                v[0] += V[d] * W[d];
+                if (mnew == 2) {
+                    v[1] += V[d] * W[ld + d];
+                    v[2] += V[ld + d] * W[ld + d];
+                }
+            }
+            block_sum_n<T>(v, 3, red);
+            if (tid == 0) {
+                G[0] = (double)v[0];
+                if (mnew == 2) {
+                    G[1] = G[MMAX] = (double)v[1];
+                    G[MMAX + 1] = (double)v[2];
+                }
+            }
+            m = mnew;
+            have_prev = false;
+        } else {
+            // ys is rewritten by the next eigensolve only after the barriers below
+            if (tid < MMAX) yps[tid] = (tid < m) ? ys[tid] : 0.0;
+            have_prev = true;
         }
-        T v3[1] = {0};
-        for (int d = tid; d < N; d += nt) v3[0] += t[d] * t[d];
-        block_sum<T, 1>(v3, tred);
-        T tn = sqrt(v3[0]);
+        // Correction: orthogonalise against V[0..m) twice, into V[m].
+        T *tv = V + (size_t)m * ld;
+        const T *tsrc = (tdst == tx) ? tx : tv;
+        for (int pass = 0; pass < 2; ++pass) {
+#pragma unroll
+            for (int i = 0; i < KRED; ++i) v[i] = 0;
+            for (int d = tid; d < N; d += nt) {
+                T td = (pass == 0) ? tsrc[d] : tv[d];
+#pragma unroll
+                for (int i = 0; i < MMAX; ++i)
+                    if (i < m) v[i] += V[(size_t)i * ld + d] * td;
+            }
+            block_sum_n<T>(v, m, red);
+            for (int d = tid; d < N; d += nt) {
+                T td = (pass == 0) ? tsrc[d] : tv[d];
+#pragma unroll
+                for (int i = 0; i < MMAX; ++i)
+                    if (i < m) td -= v[i] * V[(size_t)i * ld + d];
+                tv[d] = td;
+            }
+        }
+        v[0] = 0;
+        for (int d = tid; d < N; d += nt) v[0] += tv[d] * tv[d];
+        block_sum_n<T>(v, 1, red);
+        T tn = sqrt(v[0]);
         if (!(tn > tiny_norm<T>())) {
             if (!steer && rn > (T)tol) o.status = MBE_STATUS_MAXITER;
             break;
         }
         T tinv = (T)1 / tn;
-        for (int d = tid; d < N; d += nt) t[d] *= tinv;
+        for (int d = tid; d < N; d += nt) tv[d] *= tinv;
         __syncthreads();
-        for (int d = tid; d < N; d += nt) ht[d] = sigma_elem<T>(pb, V, Hs, t, d);
+        T *wv = W + (size_t)m * ld;
+        for (int d = tid; d < N; d += nt) wv[d] = sigma_elem<T>(pb, Vi, Hs, tv, d);
         ++o.nsig;
-        T g[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < KRED; ++i) v[i] = 0;
         for (int d = tid; d < N; d += nt) {
-            g[0] += x[d] * hx[d];
-            g[1] += x[d] * hp[d];
-            g[2] += x[d] * ht[d];
-            g[3] += p[d] * hp[d];
-            g[4] += p[d] * ht[d];
-            g[5] += t[d] * ht[d];
+            T wd = wv[d];
+#pragma unroll
+            for (int i = 0; i < MMAX + 1; ++i)
+                if (i <= m) v[i] += V[(size_t)i * ld + d] * wd;
         }
-        block_sum<T, 6>(g, tred);
-        T G[3][3];
-        G[0][0] = g[0];
-        G[0][1] = G[1][0] = g[1];
-        G[0][2] = G[2][0] = g[2];
-        G[1][1] = g[3];
-        G[1][2] = G[2][1] = g[4];
-        G[2][2] = g[5];
-        T y[3];
-        eig3<T>(G, have_p, y);
-        T w2 = y[1] * y[1] + y[2] * y[2];
-        T q0 = -w2 * y[0], q1 = y[1] - w2 * y[1], q2 = y[2] - w2 * y[2];
-        T zn = sqrt(q0 * q0 + q1 * q1 + q2 * q2);
-        bool np_ok = zn > tiny_norm<T>() * (T)1e-3;
-        T zi = np_ok ? (T)1 / zn : (T)0;
-        T y0 = y[0], y1 = y[1], y2 = y[2];
-        q0 *= zi;
-        q1 *= zi;
-        q2 *= zi;
-        T v4[2] = {0, 0};
-        for (int d = tid; d < N; d += nt) {
-            T xd = x[d], pd = p[d], td = t[d], hxd = hx[d], hpd = hp[d], htd = ht[d];
-            T nx = y0 * xd + y1 * pd + y2 * td;
-            T nhx = y0 * hxd + y1 * hpd + y2 * htd;
-            x[d] = nx;
-            hx[d] = nhx;
-            p[d] = q0 * xd + q1 * pd + q2 * td;
-            hp[d] = q0 * hxd + q1 * hpd + q2 * htd;
-            v4[0] += nx * nx;
-            v4[1] += nx * nhx;
-        }
-        have_p = np_ok;
-        block_sum<T, 2>(v4, tred);
-        T xi = (T)1 / sqrt(v4[0]);
-        for (int d = tid; d < N; d += nt) {
-            x[d] *= xi;
-            hx[d] *= xi;
-        }
-        lam = v4[1] / v4[0];
+        block_sum_n<T>(v, m + 1, red);
+        if (tid == 0)
+            for (int i = 0; i <= m; ++i) G[i * MMAX + m] = G[m * MMAX + i] = (double)v[i];
         __syncthreads();
+        ++m;
     }
-    o.lambda = (double)lam;
+    o.lambda = theta;
     o.rnorm = (double)rn;
     return o;
 }
 
-__global__ void __launch_bounds__(CTA_THREADS) k_casci_block(BatchArgs a, int bucket)
+__global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int bucket)
 {
     extern __shared__ __align__(16) char smem[];
     const int n = a.n, P = n * (n + 1) / 2;
@@ -962,6 +1179,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_casci_block(BatchArgs a, int bu
         pb.Hs64 = (double *)(slot + L.off_Hs64);
         pb.Hs32 = (float *)(slot + L.off_Hs32);
         pb.diag = (double *)(slot + L.off_diag);
+        pb.c = nullptr;
         const bool mixed = a.precision == MBE_PREC_MIXED;
         setup_problem<BlockGroup>(a, pb, mixed);
         uint32_t mphi = 0;
@@ -1016,7 +1234,7 @@ __global__ void __launch_bounds__(CTA_THREADS) k_casci_block(BatchArgs a, int bu
         int n32 = 0;
         if (mixed) {
             float *x32 = (float *)(slot + L.off_x);
-            // float views of the same slot: x in the first half of the x region
+            // narrow x in place (float view of the same region), bottom up
             for (int base = 0; base < pb.N; base += blockDim.x) {
                 int d = base + threadIdx.x;
                 double v = (d < pb.N) ? x64[d] : 0.0;
@@ -1024,11 +1242,12 @@ __global__ void __launch_bounds__(CTA_THREADS) k_casci_block(BatchArgs a, int bu
                 if (d < pb.N) x32[d] = (float)v;
                 __syncthreads();
             }
-            PhaseOut o32 = davidson_block<float>(
-                pb, x32, (float *)(slot + L.off_hx), (float *)(slot + L.off_p), (float *)(slot + L.off_hp),
-                (float *)(slot + L.off_t), (float *)(slot + L.off_ht), red, a.tol_switch, 0, a.max_iter, true);
+            PhaseOut o32 = davidson_block<float>(pb, (float *)(slot + L.off_V), (float *)(slot + L.off_W),
+                                                 L.vec / 4, x32, (float *)(slot + L.off_hx),
+                                                 (float *)(slot + L.off_t), smem, S, a.tol_switch, 0, a.max_iter,
+                                                 true);
             n32 = o32.nsig;
-            // widen x back to float64 in place, from the top down
+            // widen x back to float64 in place, top down
             for (int base = ((pb.N - 1) / (int)blockDim.x) * (int)blockDim.x; base >= 0; base -= (int)blockDim.x) {
                 int d = base + threadIdx.x;
                 float v = (d < pb.N) ? x32[d] : 0.0f;
@@ -1042,11 +1261,10 @@ __global__ void __launch_bounds__(CTA_THREADS) k_casci_block(BatchArgs a, int bu
                 __syncthreads();
             }
         }
-        pb.c = nullptr;
-        PhaseOut o64 = davidson_block<double>(
-            pb, x64, (double *)(slot + L.off_hx), (double *)(slot + L.off_p), (double *)(slot + L.off_hp),
-            (double *)(slot + L.off_t), (double *)(slot + L.off_ht), red, a.tol, mixed ? a.min_fp64 : 0,
-            a.max_iter, false);
+        PhaseOut o64 = davidson_block<double>(pb, (double *)(slot + L.off_V), (double *)(slot + L.off_W),
+                                              L.vec / 8, x64, (double *)(slot + L.off_hx),
+                                              (double *)(slot + L.off_t), smem, S, a.tol,
+                                              mixed ? a.min_fp64 : 0, a.max_iter, false);
         if (threadIdx.x == 0) {
             double e = o64.status == MBE_STATUS_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL)
                                                          : o64.lambda - ephi - a.e_ref_corr;
@@ -1194,9 +1412,8 @@ extern "C" int casci_batch(mbe_ctx *ctx, int norb, const double *h1, const doubl
                            int64_t n_tuples, const int32_t *tuples, const mbe_opts *opts, double *eps_out,
                            int32_t *status_out, int32_t *iters_out)
 {
-    MBE_CHECK(ctx != nullptr && h1 != nullptr && eri != nullptr && occ != nullptr && eps_out != nullptr &&
-                  status_out != nullptr,
-              MBE_EINVAL, "casci_batch: NULL argument");
+    MBE_CHECK(ctx != nullptr && h1 != nullptr && eri != nullptr && occ != nullptr, MBE_EINVAL,
+              "casci_batch: NULL argument");
     MBE_CHECK(norb >= 1 && norb <= MBE_MAX_NORB, MBE_EINVAL, "casci_batch: norb %d outside 1..%d", norb,
               MBE_MAX_NORB);
     MBE_CHECK(n_ref >= 0 && order >= 0 && n_tuples >= 0, MBE_EINVAL, "casci_batch: negative size");
@@ -1214,6 +1431,7 @@ extern "C" int casci_batch(mbe_ctx *ctx, int norb, const double *h1, const doubl
     MBE_CHECK(o.tol > 0 && o.tol_switch > 0 && o.max_iter >= 1 && o.fp64_final_iters >= 0, MBE_EINVAL,
               "casci_batch: bad options");
     if (n_tuples == 0) return MBE_OK;
+    MBE_CHECK(eps_out != nullptr && status_out != nullptr, MBE_EINVAL, "casci_batch: NULL output");
     MBE_CU(cudaSetDevice(ctx->device));
 
     BatchArgs a;

@@ -115,7 +115,7 @@ void mbe_default_opts(mbe_opts *o)
     o->precision = MBE_PREC_FP64;
     o->tol = 1e-6;
     o->tol_switch = 1e-4;
-    o->max_iter = 200;
+    o->max_iter = 500;
     o->fp64_final_iters = 2;
 }
 
