@@ -218,6 +218,43 @@ int casci_sigma(mbe_ctx *ctx, int norb, const double *h1, const double *eri, con
                 int n_cas, const int32_t *cas_orbs, const double *c, double *sigma,
                 double *diag);
 
+/*
+ * Allocation-free variant of casci_sigma.  The paper has no counterpart: it
+ * serves callers that cannot allocate device memory when they call, such as a
+ * host application whose memory is owned by its own pool or allocator, code
+ * running under a hard real-time or stream-capture discipline in which
+ * cudaMalloc would stall or be illegal, or a plug-in that must not grow device
+ * memory behind its host's back.
+ *
+ * The call computes the same sigma = H_A c (and the diagonal) as casci_sigma,
+ * for the sector with n_el alpha and n_el beta electrons in the active space
+ * cas_orbs (occ still defines the frozen core), but it allocates nothing: it
+ * calls no cudaMalloc, cudaFree or allocating library routine and needs no
+ * mbe_ctx.  Its scratch (core Fock matrix, string tables, packed integrals,
+ * one-spin Hamiltonian, and the diagonal when diag is NULL) is one fixed
+ * file-scope device array of MBE_NOALLOC_SCRATCH_BYTES, which every GPU that
+ * loads the library holds until the process exits.
+ *   device         CUDA device to run on (made current for the call, then restored)
+ *   cuda_stream    cudaStream_t the work is issued on (NULL = legacy default stream)
+ *   n_cas <= MBE_NOALLOC_MAX_CAS; larger problems, or any whose scratch would
+ *   exceed MBE_NOALLOC_SCRATCH_BYTES, are rejected with MBE_EUNSUPPORTED and a
+ *   message saying so.  The caller still passes and owns inputs and outputs
+ *   (device pointers, same layouts as casci_sigma).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  Every call reuses the same array and
+ * leaves the last call's contents in it; each call fully rewrites what it reads,
+ * so nothing carries over.  Calls whose work overlaps on the GPU (other streams,
+ * other host threads) race on the array: serialise them.
+ * Errors: MBE_EINVAL, MBE_EUNSUPPORTED, MBE_ECUDA.  Asynchronous on cuda_stream.
+ */
+#define MBE_NOALLOC_MAX_CAS 10
+#define MBE_NOALLOC_SCRATCH_BYTES (2u << 20) /* 2 MiB per device */
+#define MBE_MAX_DEVICES 64
+int casci_sigma_noalloc(int device, void *cuda_stream, int norb, const double *h1, const double *eri,
+                        const uint8_t *occ, int n_cas, const int32_t *cas_orbs, int n_el, const double *c,
+                        double *sigma, double *diag);
+
 /* ------------------------------------------------------------------ a8-a9: Eqs. 2, 1 */
 
 /*

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "NONFINITE", 3: "BADINPUT"}
 EXPORTS = ("mbe_default_opts", "mbe_ctx_create", "mbe_ctx_set_stream", "mbe_ctx_destroy",
            "mbe_last_error", "mbe_ctx_sync", "mbe_ctx_launches", "mbe_ctx_set_timing",
            "mbe_ctx_timings", "mbe_tuples", "mbe_string_table", "mbe_phi_energy",
-           "casci_batch", "casci_sigma", "mbe_increments", "mbe_total")
+           "casci_batch", "casci_sigma", "casci_sigma_noalloc", "mbe_increments", "mbe_total")
 
 
 class MbeOpts(ctypes.Structure):
@@ -89,6 +89,8 @@ def lib() -> ctypes.CDLL:
                               P, P, P]
     L.casci_sigma.restype = i32
     L.casci_sigma.argtypes = [P, i32, P, P, P, i32, P, P, P, P]
+    L.casci_sigma_noalloc.restype = i32
+    L.casci_sigma_noalloc.argtypes = [i32, P, i32, P, P, P, i32, P, i32, P, P, P]
     L.mbe_increments.restype = i32
     L.mbe_increments.argtypes = [P, i32, i64, P, P, i32, P, P, P, P]
     L.mbe_total.restype = i32

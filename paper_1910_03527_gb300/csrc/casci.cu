@@ -25,6 +25,7 @@
 // the vectors and Hs in a per-block slot of the context workspace.  Both are
 // persistent kernels that pull tuples from an atomic counter per bucket.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -1691,4 +1692,114 @@ extern "C" int casci_sigma(mbe_ctx *ctx, int norb, const double *h1, const doubl
     MBE_CU(cudaGetLastError());
     ctx->launches += 3;
     return MBE_OK;
+}
+
+// ------------------------------------------------------------------ allocation-free sigma
+//
+// casci_sigma_noalloc: the same sigma product as casci_sigma for callers that
+// cannot allocate device memory at call time (see include/mbe.h).  Its scratch
+// (core Fock matrix, string tables, packed integrals, Hs and, when the caller
+// passes no diag buffer, the diagonal) lives in one fixed file-scope device
+// array instead of the context workspace.
+
+namespace mbe {
+
+__global__ void k_string_table(int n, int k, int64_t ns, int r, uint32_t *strings, int32_t *table);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MBE_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch per device, looked up once with that
+// device current.  In host code the symbol itself is only a host-side handle.
+static std::mutex g_noalloc_mutex;
+static void *g_noalloc_addr[MBE_MAX_DEVICES];
+
+static int noalloc_scratch(int device, void **out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+        g_noalloc_addr[device] = p;
+    }
+    *out = g_noalloc_addr[device];
+    return MBE_OK;
+}
+
+}  // namespace mbe
+
+extern "C" int casci_sigma_noalloc(int device, void *cuda_stream, int norb, const double *h1, const double *eri,
+                                   const uint8_t *occ, int n_cas, const int32_t *cas_orbs, int n_el,
+                                   const double *c, double *sigma, double *diag)
+{
+    MBE_CHECK(h1 && eri && occ && cas_orbs && c && sigma, MBE_EINVAL, "casci_sigma_noalloc: NULL argument");
+    MBE_CHECK(device >= 0 && device < MBE_MAX_DEVICES, MBE_EINVAL, "casci_sigma_noalloc: device %d", device);
+    MBE_CHECK(norb >= 1 && norb <= MBE_MAX_NORB, MBE_EINVAL, "casci_sigma_noalloc: norb %d", norb);
+    MBE_CHECK(n_cas >= 1 && n_cas <= norb, MBE_EINVAL, "casci_sigma_noalloc: n_cas %d", n_cas);
+    MBE_CHECK(n_el >= 0 && n_el <= n_cas, MBE_EINVAL, "casci_sigma_noalloc: n_el %d outside 0..%d", n_el, n_cas);
+    MBE_CHECK(n_cas <= MBE_NOALLOC_MAX_CAS, MBE_EUNSUPPORTED,
+              "casci_sigma_noalloc: n_cas %d exceeds the allocation-free limit of %d orbitals", n_cas,
+              MBE_NOALLOC_MAX_CAS);
+    std::vector<int> A(cas_orbs, cas_orbs + n_cas);
+    std::sort(A.begin(), A.end());
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int i = 0; i < n_cas; ++i) {
+        MBE_CHECK(A[i] >= 0 && A[i] < norb && (i == 0 || A[i] != A[i - 1]), MBE_EINVAL,
+                  "casci_sigma_noalloc: active orbital %d out of range or repeated", A[i]);
+        a.ref[i] = A[i];
+    }
+    const int64_t ns = binom(n_cas, n_el);
+    const int r = n_el * (n_cas - n_el + 1);
+    const int P = n_cas * (n_cas + 1) / 2;
+    const int64_t N = ns * ns;
+    const size_t hs_elems = (size_t)ns * odd_stride((int)ns);
+    size_t need = align256((size_t)norb * norb * 8) + align256((size_t)ns * 4) +
+                  align256((size_t)ns * (r > 0 ? r : 1) * 4) + align256((size_t)P * P * 8) + align256(hs_elems * 8) +
+                  (diag ? 0 : align256((size_t)N * 8));
+    MBE_CHECK(need <= MBE_NOALLOC_SCRATCH_BYTES, MBE_EUNSUPPORTED,
+              "casci_sigma_noalloc: needs %zu bytes of scratch, more than the fixed %zu", need,
+              (size_t)MBE_NOALLOC_SCRATCH_BYTES);
+    int prev = 0;
+    MBE_CU(cudaGetDevice(&prev));
+    if (prev != device) MBE_CU(cudaSetDevice(device));
+    void *scratch = nullptr;
+    int rc = noalloc_scratch(device, &scratch);
+    if (rc == MBE_OK) {
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        Bump bump(scratch);
+        double *F = bump.take<double>((size_t)norb * norb);
+        uint32_t *strings = bump.take<uint32_t>((size_t)ns);
+        int32_t *table = bump.take<int32_t>((size_t)ns * (r > 0 ? r : 1));
+        double *V = bump.take<double>((size_t)P * P);
+        double *Hs = bump.take<double>(hs_elems);
+        double *dg = diag ? diag : bump.take<double>((size_t)N);
+        a.norb = norb;
+        a.n = n_cas;
+        a.n_ref = n_cas;
+        a.order = 0;
+        a.eri = eri;
+        a.occ = occ;
+        a.F = F;
+        a.n_tuples = 1;
+        ClassInfo ci{strings, table, (int)ns, r};
+        k_string_table<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(n_cas, n_el, ns, r, strings, table);
+        k_core_fock<<<(norb * norb + 127) / 128, 128, 0, st>>>(norb, h1, eri, occ, F);
+        BlockSmem S = block_smem(n_cas);
+        cudaError_t e = cudaFuncSetAttribute(k_sigma_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, S.bytes);
+        if (e == cudaSuccess) {
+            k_sigma_setup<<<1, CTA_THREADS, S.bytes, st>>>(a, ci, V, Hs, dg);
+            int smem = P * P * 8;
+            e = cudaFuncSetAttribute(k_sigma_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        }
+        if (e == cudaSuccess) {
+            int64_t blocks = (N + CTA_THREADS - 1) / CTA_THREADS;
+            int grid = (int)std::min<int64_t>(blocks, 4096);
+            k_sigma_apply<<<grid, CTA_THREADS, P * P * 8, st>>>(n_cas, ci, V, Hs, c, sigma);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) rc = cuda_fail(e, "casci_sigma_noalloc launch", __FILE__, __LINE__);
+    }
+    if (prev != device) cudaSetDevice(prev);
+    return rc;
 }
