@@ -90,7 +90,7 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -239,14 +239,12 @@ def run_ours(args):
         step(fp64)
     torch.cuda.synchronize()
 
-    def timed(opts, sampler=None):
+    def timed(opts):
         barrier()
         torch.cuda.synchronize()
         ctx.take_timings()
         ctx.set_timing(True)
         l0 = ctx.launches()
-        if sampler:
-            sampler.start()
         evs, out = [], None
         for _ in range(args.steps):
             flush.zero_()
@@ -257,15 +255,17 @@ def run_ours(args):
             evs.append((s, e))
         torch.cuda.synchronize()
         barrier()
-        clocks = sampler.stop() if sampler else None
         launches = ctx.launches() - l0
         recs = ctx.take_timings()
         ctx.set_timing(False)
         ms = [s.elapsed_time(e) for s, e in evs]
-        return ms, out, recs, launches, clocks
+        return ms, out, recs, launches
 
-    ms_mix, out_mix, recs_mix, launches, clocks = timed(mixed, ClockSampler(local))
-    ms_64, out_64, recs_64, _, _ = timed(fp64)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms_mix, out_mix, recs_mix, launches = timed(mixed)
+    ms_64, out_64, recs_64, _ = timed(fp64)
+    clocks = sampler.stop()
 
     tot_mix = torch.tensor([sum(ms_mix)], dtype=torch.float64, device=dev)
     tot_64 = torch.tensor([sum(ms_64)], dtype=torch.float64, device=dev)
@@ -284,40 +284,53 @@ def run_ours(args):
                 if a.numel() > 0] + [0.0])
     bad = sum(int((s != 0).sum().item()) for s in out_mix["status"] + out_64["status"])
 
+    def sigma_counts(out):
+        it = torch.cat([x for x in out["iters"] if x.numel() > 0])
+        n64 = ((it >> 16) & 0xffff).double().mean().item()
+        n32 = (it & 0xffff).double().mean().item()
+        return {"fp64_sigma_per_tuple": n64, "fp32_sigma_per_tuple": n32}
+
+    solver_stats = {"mixed": sigma_counts(out_mix), "fp64": sigma_counts(out_64)}
+
     # ---- roofline of the dominant solver kernel (per launch, CUDA events inside the library)
     occ_np = np.asarray(w.occ)
-    per_bucket = {}
-    for (order, solver, dpl, ms) in recs_mix:
-        per_bucket.setdefault((order, solver, dpl), []).append(ms)
-    key = max(per_bucket, key=lambda k: sum(per_bucket[k]))
-    order, solver, dpl = key
-    i = w.orders.index(order)
-    tup = out_mix["tuples"][i].cpu().numpy()
-    iters = out_mix["iters"][i].cpu().numpy()
-    kk = occ_np[tup].sum(axis=1)
-    n = len(w.ref) + order
-    f64 = f32 = 0.0
-    for k in np.unique(kk):
-        if solver_bucket(n, int(k)) != (solver, dpl):
-            continue
-        sel = kk == k
-        per_it = sigma_flops_per_det(n, int(k)) + DAVIDSON_FLOPS_PER_DET
-        ndet = math.comb(n, int(k)) ** 2
-        f64 += float(((iters[sel] >> 16) & 0xffff).sum()) * per_it * ndet
-        f32 += float((iters[sel] & 0xffff).sum()) * per_it * ndet
-    launch_ms = statistics.mean(per_bucket[key])
-    t_s = launch_ms / 1e3
-    achieved = (f64 + f32 * PEAK_FP64_TFLOPS / PEAK_FP32_TFLOPS) / t_s / 1e12
-    kname = f"k_casci_warp<{dpl}>" if solver == 0 else "k_casci_block"
-    roofline = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS,
+
+    def roofline_of(recs, out, total_ms):
+        per_bucket = {}
+        for (order, solver, dpl, ms) in recs:
+            per_bucket.setdefault((order, solver, dpl), []).append(ms)
+        key = max(per_bucket, key=lambda k: sum(per_bucket[k]))
+        order, solver, dpl = key
+        i = w.orders.index(order)
+        tup = out["tuples"][i].cpu().numpy()
+        iters = out["iters"][i].cpu().numpy()
+        kk = occ_np[tup].sum(axis=1)
+        n = len(w.ref) + order
+        f64 = f32 = 0.0
+        for k in np.unique(kk):
+            if solver_bucket(n, int(k)) != (solver, dpl):
+                continue
+            sel = kk == k
+            per_it = sigma_flops_per_det(n, int(k)) + DAVIDSON_FLOPS_PER_DET
+            ndet = math.comb(n, int(k)) ** 2
+            f64 += float(((iters[sel] >> 16) & 0xffff).sum()) * per_it * ndet
+            f32 += float((iters[sel] & 0xffff).sum()) * per_it * ndet
+        launch_ms = statistics.mean(per_bucket[key])
+        t_s = launch_ms / 1e3
+        achieved = (f64 + f32 * PEAK_FP64_TFLOPS / PEAK_FP32_TFLOPS) / t_s / 1e12
+        kname = f"k_casci_warp<{dpl}>" if solver == 0 else "k_casci_block"
+        return {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS,
                 "unit": "TFLOP/s (float64-equivalent: float32 flops weighted by the "
                         "float64:float32 peak ratio; peaks derived from unit counts at 2070 MHz)",
                 "frac": achieved / PEAK_FP64_TFLOPS,
-                "traffic": recorded_traffic(f"{kname}:order{order}"),
+                "traffic": recorded_traffic(f"{kname}:order{order}:{'mixed' if f32 > 0 else 'fp64'}"),
                 "kernel": kname, "launch": f"order {order} solver launch",
                 "ms_per_launch": launch_ms, "fp64_flop_per_launch": f64, "fp32_flop_per_launch": f32,
                 "fp64_tflops": f64 / t_s / 1e12, "fp32_tflops": f32 / t_s / 1e12,
-                "share_of_step": sum(per_bucket[key]) / sum(ms_mix)}
+                "share_of_step": sum(per_bucket[key]) / total_ms}
+
+    roofline = roofline_of(recs_mix, out_mix, sum(ms_mix))
+    roofline_64 = roofline_of(recs_64, out_64, sum(ms_64))
 
     # ---- end to end through the public API with host inputs
     h1_h = torch.tensor(w.h1).pin_memory()
@@ -346,14 +359,16 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step_mix, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "tuples_per_step": n_tuples, "orders": "1-6",
-                   "precision": "mixed (float32 Davidson to residual 1e-4, then >= 2 float64 iterations "
+                   "precision": "mixed (float32 Davidson to residual 1e-5, then >= 2 float64 iterations "
                                 "to residual 1e-6)",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"{ws} independent replica(s), no collective"},
-        "fp64": {"value": value_64, "unit": UNIT, "ms_per_step": ms_step_64, "dtype": "f64"},
+        "fp64": {"value": value_64, "unit": UNIT, "ms_per_step": ms_step_64, "dtype": "f64",
+                 "roofline": roofline_64},
         "accuracy": {"max_abs_eps_mixed_minus_fp64_Eh": diff, "non_ok_status": bad,
                      "e_total_mixed": float(out_mix["e_total"].item()),
                      "e_total_fp64": float(out_64["e_total"].item())},
+        "solver": solver_stats,
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(launches),

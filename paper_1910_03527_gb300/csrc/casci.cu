@@ -128,6 +128,7 @@ struct Problem {
     float *Hs32;          // [Ns*HSS]
     double *diag;         // [N]
     void *c;              // [N] vector sigma reads (T)
+    void *sbuf;           // [N] sigma output staging (warp solver)
 };
 
 __host__ __device__ inline int odd_stride(int x) { return x | 1; }
@@ -241,6 +242,14 @@ __device__ void setup_problem(const BatchArgs &a, Problem &pb, bool want32)
     G::sync();
 }
 
+// v with its sign bit flipped when neg is 1 (an integer operation, so that the
+// signed product below stays one fused multiply-add).
+__device__ inline double flip_if(double v, int neg)
+{
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
+}
+__device__ inline float flip_if(float v, int neg) { return __int_as_float(__float_as_int(v) ^ (neg << 31)); }
+
 // a5: one element of sigma = H c.
 template <typename T>
 __device__ inline T sigma_elem(const Problem &pb, const T *__restrict__ V, const T *__restrict__ Hs,
@@ -251,23 +260,34 @@ __device__ inline T sigma_elem(const Problem &pb, const T *__restrict__ V, const
     const T *ha = Hs + ia * pb.HSS;
     const T *hb = Hs + ib * pb.HSS;
     const T *crow = c + ia * Ns;
-    T acc = 0;
-    for (int J = 0; J < Ns; ++J) acc += ha[J] * c[J * Ns + ib] + hb[J] * crow[J];
+    // Two independent accumulators per sum keep two FMA chains in flight.
+    T acc0 = 0, acc1 = 0;
+    for (int J = 0; J < Ns; ++J) {
+        acc0 = fma(ha[J], c[J * Ns + ib], acc0);
+        acc1 = fma(hb[J], crow[J], acc1);
+    }
     const int32_t *ta = pb.tab + ia * pb.RS;
     const int32_t *tb = pb.tab + ib * pb.RS;
-    for (int x = 0; x < pb.R; ++x) {
+    const int R = pb.R;
+    for (int x = 0; x < R; ++x) {
         int ea = ta[x];
         const T *vrow = V + entry_pair(ea) * pb.P;
         const T *cr = c + entry_J(ea) * Ns;
-        T s = 0;
-        for (int y = 0; y < pb.R; ++y) {
-            int eb = tb[y];
-            T v = vrow[entry_pair(eb)] * cr[entry_J(eb)];
-            s = entry_neg(eb) ? s - v : s + v;
+        T s0 = 0, s1 = 0;
+        int y = 0;
+        for (; y + 1 < R; y += 2) {
+            int e0 = tb[y], e1 = tb[y + 1];
+            s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), cr[entry_J(e0)], s0);
+            s1 = fma(flip_if(vrow[entry_pair(e1)], entry_neg(e1)), cr[entry_J(e1)], s1);
         }
-        acc = entry_neg(ea) ? acc - s : acc + s;
+        if (y < R) {
+            int e0 = tb[y];
+            s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), cr[entry_J(e0)], s0);
+        }
+        T s = s0 + s1;
+        if (x & 1) acc1 += flip_if(s, entry_neg(ea)); else acc0 += flip_if(s, entry_neg(ea));
     }
-    return acc;
+    return acc0 + acc1;
 }
 
 // Lowest eigenpair of the symmetric 3x3 Rayleigh-Ritz matrix G (m = 2 or 3 active
@@ -309,16 +329,19 @@ __device__ inline void eig3(const T (&G)[3][3], bool have_p, T (&y)[3])
             Vv[i][j] = (i == j) ? 1.0f : 0.0f;
         }
     if (!have_p) {
+        // Only x and t span the subspace: a single rotation of the {0, 2} block.
         A[0][1] = A[1][0] = A[1][2] = A[2][1] = 0.0f;
-        A[1][1] = 3.0e30f;
-    }
-    for (int sweep = 0; sweep < 6; ++sweep) {
-        float off = fabsf(A[0][1]) + fabsf(A[0][2]) + fabsf(A[1][2]);
-        float dia = fabsf(A[0][0]) + fabsf(A[1][1]) + fabsf(A[2][2]);
-        if (off <= 1e-10f * dia || off < 1e-36f) break;
-        rotate3(A, Vv, 0, 1);
         rotate3(A, Vv, 0, 2);
-        rotate3(A, Vv, 1, 2);
+        A[1][1] = 3.0e38f;
+    } else {
+        for (int sweep = 0; sweep < 6; ++sweep) {
+            float off = fabsf(A[0][1]) + fabsf(A[0][2]) + fabsf(A[1][2]);
+            float dia = fabsf(A[0][0]) + fabsf(A[1][1]) + fabsf(A[2][2]);
+            if (off <= 1e-10f * dia || off < 1e-36f) break;
+            rotate3(A, Vv, 0, 1);
+            rotate3(A, Vv, 0, 2);
+            rotate3(A, Vv, 1, 2);
+        }
     }
     int m = 0;
     if (A[1][1] < A[m][m]) m = 1;
@@ -398,13 +421,17 @@ struct PhaseOut {
 // ------------------------------------------------------------------ warp solver
 
 template <typename T, int DPL>
-__device__ inline void sigma_warp(const Problem &pb, const T *V, const T *Hs, const T *c, T (&out)[DPL])
+__device__ inline void sigma_warp(const Problem &pb, const T *V, const T *Hs, const T *c, T *sbuf, T (&out)[DPL])
 {
     const int lane = threadIdx.x & 31;
+    // One compact loop (not unrolled DPL times) keeps the kernel small enough for
+    // the instruction cache; each lane reads back only the elements it wrote.
+#pragma unroll 1
+    for (int d = lane; d < pb.N; d += 32) sbuf[d] = sigma_elem<T>(pb, V, Hs, c, d);
 #pragma unroll
     for (int j = 0; j < DPL; ++j) {
         int d = lane + 32 * j;
-        out[j] = (d < pb.N) ? sigma_elem<T>(pb, V, Hs, c, d) : (T)0;
+        out[j] = (d < pb.N) ? sbuf[d] : (T)0;
     }
 }
 
@@ -424,6 +451,7 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
     const T *V = sizeof(T) == 8 ? (const T *)pb.V64 : (const T *)pb.V32;
     const T *Hs = sizeof(T) == 8 ? (const T *)pb.Hs64 : (const T *)pb.Hs32;
     T *c = (T *)pb.c;
+    T *sbuf = (T *)pb.sbuf;
     T hx[DPL], p[DPL], hp[DPL], ht[DPL];
     PhaseOut o;
     o.nsig = 0;
@@ -443,7 +471,7 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
         hp[j] = 0;
     }
     __syncwarp();
-    sigma_warp<T, DPL>(pb, V, Hs, c, hx);
+    sigma_warp<T, DPL>(pb, V, Hs, c, sbuf, hx);
     ++o.nsig;
     __syncwarp();
     T xh = 0;
@@ -523,7 +551,7 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
             if (d < pb.N) c[d] *= tinv;
         }
         __syncwarp();
-        sigma_warp<T, DPL>(pb, V, Hs, c, ht);
+        sigma_warp<T, DPL>(pb, V, Hs, c, sbuf, ht);
         ++o.nsig;
         __syncwarp();
         T g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0;
@@ -590,7 +618,7 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
 }
 
 struct WarpLayout {
-    int off_A, off_pp, off_h, off_hp, off_V64, off_V32, off_Hs64, off_Hs32, off_diag, off_c, off_str,
+    int off_A, off_pp, off_h, off_hp, off_V64, off_V32, off_Hs64, off_Hs32, off_diag, off_c, off_s, off_str,
         off_tab, bytes;
 };
 
@@ -611,6 +639,7 @@ __host__ __device__ inline WarpLayout warp_layout(int n, int ns, int r, int N)
     L.off_Hs32 = o; o = al16(o + 4 * ns * HSS);
     L.off_diag = o; o = al16(o + 8 * N);
     L.off_c = o; o = al16(o + 8 * N);
+    L.off_s = o; o = al16(o + 8 * N);
     L.off_str = o; o = al16(o + 4 * ns);
     L.off_tab = o; o = al16(o + 4 * ns * RS);
     L.bytes = o;
@@ -674,6 +703,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
         pb.Hs32 = (float *)(ws + L.off_Hs32);
         pb.diag = (double *)(ws + L.off_diag);
         pb.c = (void *)(ws + L.off_c);
+        pb.sbuf = (void *)(ws + L.off_s);
         __syncwarp();
         const bool mixed = a.precision == MBE_PREC_MIXED;
         setup_problem<WarpGroup>(a, pb, mixed);
