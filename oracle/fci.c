@@ -327,3 +327,64 @@ int oracle_sigma_rows(int n, int na, int nb, const double *h, const double *eri,
     space_free(&s);
     return 0;
 }
+
+/*
+ * Spin-free reduced density matrices of the state c in the (na, nb) sector,
+ * by explicit action of creation and annihilation operators on determinants:
+ *   gamma[p*n+q]             = sum_s      <c| a+_ps a_qs |c>
+ *   Gamma[((p*n+q)*n+r)*n+s] = sum_{s,t}  <c| a+_ps a+_rt a_st a_qs |c>
+ * (chemists' order, so that E = sum h_pq gamma_pq + 1/2 sum (pq|rs) Gamma_pqrs).
+ * Gamma may be NULL.  Operators act rightmost first, each with its
+ * Jordan-Wigner sign.
+ */
+int oracle_rdm12(int n, int na, int nb, const double *c, double *gamma, double *Gamma)
+{
+    space_t s;
+    if (space_init(&s, n, na, nb)) return -1;
+    int64_t N = s.Na * s.Nb;
+    for (int i = 0; i < n * n; ++i) gamma[i] = 0.0;
+    if (Gamma)
+        for (int64_t i = 0; i < (int64_t)n * n * n * n; ++i) Gamma[i] = 0.0;
+    int m = 2 * n;
+    for (int64_t j = 0; j < N; ++j) {
+        double cj = c[j];
+        if (cj == 0.0) continue;
+        word J = det_word(&s, j);
+        for (int Q = 0; Q < m; ++Q) {
+            if (!((J >> Q) & 1)) continue;
+            int g1 = jw_sign(J, Q);
+            word d1 = J & ~(((word)1) << Q);
+            /* one-body: a+_P a_Q, same spin */
+            for (int P = 0; P < m; ++P) {
+                if (P / n != Q / n || ((d1 >> P) & 1)) continue;
+                int g2 = jw_sign(d1, P);
+                word I = d1 | (((word)1) << P);
+                int64_t i = det_index(&s, I);
+                if (i >= 0) gamma[(P % n) * n + (Q % n)] += c[i] * g1 * g2 * cj;
+            }
+            if (!Gamma) continue;
+            /* two-body: a+_P a+_R a_S a_Q, spin(P) = spin(Q), spin(R) = spin(S) */
+            for (int S = 0; S < m; ++S) {
+                if (!((d1 >> S) & 1)) continue;
+                int g2 = jw_sign(d1, S);
+                word d2 = d1 & ~(((word)1) << S);
+                for (int R = 0; R < m; ++R) {
+                    if (R / n != S / n || ((d2 >> R) & 1)) continue;
+                    int g3 = jw_sign(d2, R);
+                    word d3 = d2 | (((word)1) << R);
+                    for (int P = 0; P < m; ++P) {
+                        if (P / n != Q / n || ((d3 >> P) & 1)) continue;
+                        int g4 = jw_sign(d3, P);
+                        word I = d3 | (((word)1) << P);
+                        int64_t i = det_index(&s, I);
+                        if (i < 0) continue;
+                        int p = P % n, q = Q % n, r = R % n, ss = S % n;
+                        Gamma[(((int64_t)p * n + q) * n + r) * n + ss] += c[i] * g1 * g2 * g3 * g4 * cj;
+                    }
+                }
+            }
+        }
+    }
+    space_free(&s);
+    return 0;
+}

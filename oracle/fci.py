@@ -48,6 +48,8 @@ def lib():
     L.oracle_h_coo.argtypes = [i32, i32, i32, P, P, i64, P, P, P]
     L.oracle_sigma.restype = i32
     L.oracle_sigma.argtypes = [i32, i32, i32, P, P, P, P]
+    L.oracle_rdm12.restype = i32
+    L.oracle_rdm12.argtypes = [i32, i32, i32, P, P, P]
     L.oracle_sigma_rows.restype = i32
     L.oracle_sigma_rows.argtypes = [i32, i32, i32, P, P, P, i64, P, P]
     return L
@@ -140,6 +142,15 @@ def sigma_rows(h: np.ndarray, eri: np.ndarray, na: int, nb: int, c: np.ndarray,
     assert lib().oracle_sigma_rows(h.shape[0], na, nb, _ptr(h), _ptr(eri), _ptr(c), len(rows),
                                    _ptr(rows), _ptr(out)) == 0
     return out[: len(rows)]
+
+
+def rdm12(n: int, na: int, nb: int, c: np.ndarray, two_body: bool = True):
+    """Spin-free 1-RDM gamma[p, q] and 2-RDM Gamma[p, q, r, s] (chemists' order) of c."""
+    c = _c(c)
+    g = np.zeros(n * n)
+    G = np.zeros(n ** 4) if two_body else None
+    assert lib().oracle_rdm12(n, na, nb, _ptr(c), _ptr(g), _ptr(G) if two_body else None) == 0
+    return g.reshape(n, n), (G.reshape(n, n, n, n) if two_body else None)
 
 
 def lowest_eigenpair(h: np.ndarray, eri: np.ndarray, na: int, nb: int, tol: float = 1e-13,
