@@ -255,6 +255,57 @@ int casci_sigma_noalloc(int device, void *cuda_stream, int norb, const double *h
                         const uint8_t *occ, int n_cas, const int32_t *cas_orbs, int n_el, const double *c,
                         double *sigma, double *diag);
 
+/* ------------------------------------------------------------------ a10: adjoint */
+
+/*
+ * Adjoint weights of the increment recursion.  The paper defines the energy
+ * only; its gradient follows from the linearity of Eq. 2: E_MBE - E_CAS(R) =
+ * sum_S w(S) eps(S) over the computed tuples, with
+ *     w(S) = 1 - sum over computed proper supersets U of S of w(U),
+ * the transpose of Eq. 2 (a skipped tuple is absent, as in Eq. 2).  Orders are
+ * processed from n_orders down to 1; supersets are enumerated in a fixed order,
+ * so the result is deterministic.
+ *   n_tuples [n_orders], tuples [n_orders]  host arrays (tuples: device pointers to
+ *                                           lexicographic order-m lists, m = 1..n_orders)
+ *   exp_orbs [n_exp]                        host, the expansion space
+ *   weights [n_orders]                      host array of device pointers, out
+ * Errors: MBE_EINVAL, MBE_ECUDA.
+ */
+int mbe_weights(mbe_ctx *ctx, int n_orders, const int64_t *n_tuples, const int32_t *const *tuples,
+                int n_exp, const int32_t *exp_orbs, double *const *weights);
+
+/*
+ * Weighted Hellmann-Feynman gradients of tuple CASCI energies (the adjoint of
+ * casci_batch).  Re-solves every tuple as casci_batch does (same opts; use a
+ * tighter tol for gradients: the density matrices are first-order in the
+ * eigenvector error), forms the spin-free 1-RDM (and 2-RDM when grad_eri is not
+ * NULL) of the converged state from the replacement lists, and adds
+ *     weights[t] * ( dE_CAS(R u tuple_t)/dtheta - dE_Phi/dtheta )
+ * to the gradients, theta = h_pq (dE/dh_pq = gamma_pq) and theta = (pq|rs)
+ * (dE/d(pq|rs) = 1/2 Gamma_pqrs), every tensor element treated as independent;
+ * frozen-core contributions (core-core cancel against Phi, core-active ones are
+ * 2 gamma_pq on (cc|pq), (pq|cc) and -gamma_pq on (cq|pc), (pc|cq)) included.
+ *   same inputs as casci_batch (order 0 with tuples NULL: the CAS is R)
+ *   weights [n_tuples]   device, or NULL for all ones
+ *   grad_h1 [norb^2]     device, accumulated (+=); atomics, so the summation order
+ *                        (last bits) is not deterministic
+ *   grad_eri [norb^4]    device or NULL, accumulated (+=); needs |R| + order <= 10
+ *   status_out [n_tuples] device or NULL
+ * Errors: as casci_batch; MBE_EUNSUPPORTED for the 2-RDM beyond 10 orbitals.
+ */
+int casci_rdm_batch(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
+                    int n_ref, const int32_t *ref_orbs, int order, int64_t n_tuples, const int32_t *tuples,
+                    const mbe_opts *opts, const double *weights, double *grad_h1, double *grad_eri,
+                    int32_t *status_out);
+
+/*
+ * Adds scale * dE_Phi/dtheta: 2 scale on (i,i) of grad_h1 for i in O, and on
+ * grad_eri (if not NULL) 2 scale on (ii|jj), scale on (ii|ii), -scale on (ij|ji),
+ * i != j in O.  occ, grad_h1, grad_eri device.
+ */
+int mbe_phi_gradient(mbe_ctx *ctx, int norb, const uint8_t *occ, double scale, double *grad_h1,
+                     double *grad_eri);
+
 /* ------------------------------------------------------------------ a8-a9: Eqs. 2, 1 */
 
 /*

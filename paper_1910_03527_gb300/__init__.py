@@ -10,11 +10,13 @@ increments -> totals).
 from .binding import (  # noqa: F401
     EXPORTS,
     Context,
+    MBEEnergy,
     MbeError,
     Opts,
     STATUS_NAMES,
     lib,
     library_path,
+    mbe_gradient,
     run_mbe,
 )
 from ._build import build  # noqa: F401

@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "NONFINITE", 3: "BADINPUT"}
 EXPORTS = ("mbe_default_opts", "mbe_ctx_create", "mbe_ctx_set_stream", "mbe_ctx_destroy",
            "mbe_last_error", "mbe_ctx_sync", "mbe_ctx_launches", "mbe_ctx_set_timing",
            "mbe_ctx_timings", "mbe_tuples", "mbe_string_table", "mbe_phi_energy",
-           "casci_batch", "casci_sigma", "casci_sigma_noalloc", "mbe_increments", "mbe_total")
+           "casci_batch", "casci_sigma", "casci_sigma_noalloc", "mbe_increments", "mbe_total",
+           "mbe_weights", "casci_rdm_batch", "mbe_phi_gradient")
 
 
 class MbeOpts(ctypes.Structure):
@@ -95,6 +96,12 @@ def lib() -> ctypes.CDLL:
     L.mbe_increments.argtypes = [P, i32, i64, P, P, i32, P, P, P, P]
     L.mbe_total.restype = i32
     L.mbe_total.argtypes = [P, i32, P, P, P, dbl, P, P]
+    L.mbe_weights.restype = i32
+    L.mbe_weights.argtypes = [P, i32, P, P, i32, P, P]
+    L.casci_rdm_batch.restype = i32
+    L.casci_rdm_batch.argtypes = [P, i32, P, P, P, i32, P, i32, i64, P, ctypes.POINTER(MbeOpts), P, P, P, P]
+    L.mbe_phi_gradient.restype = i32
+    L.mbe_phi_gradient.argtypes = [P, i32, P, dbl, P, P]
     return L
 
 
@@ -293,6 +300,96 @@ class Context:
         _check(lib().mbe_total(self._h, n, counts, ip, self._p(e_phi), float(e_ref_corr),
                                self._p(e_order), self._p(e_total)), "mbe_total")
         return e_order[:n], e_total
+
+    def mbe_weights(self, tuples: List[torch.Tensor], exp: Sequence[int]) -> List[torch.Tensor]:
+        """Adjoint weights w(S) of every tuple of orders 1..len(tuples)."""
+        n = len(tuples)
+        out = [self._empty((t.shape[0],), torch.float64) for t in tuples]
+        counts = (ctypes.c_int64 * max(n, 1))(*[int(t.shape[0]) for t in tuples])
+        tp = (ctypes.c_void_p * max(n, 1))(*[self._p(t) for t in tuples])
+        wp = (ctypes.c_void_p * max(n, 1))(*[self._p(t) for t in out])
+        for t in tuples:
+            self._dev(t, torch.int32, "tuples")
+        _check(lib().mbe_weights(self._h, n, counts, tp, len(exp), _i32_host(exp), wp), "mbe_weights")
+        return out
+
+    def casci_rdm_batch(self, h1, eri, occ, ref: Sequence[int], order: int, tuples: Optional[torch.Tensor],
+                        weights: Optional[torch.Tensor], grad_h1: torch.Tensor,
+                        grad_eri: Optional[torch.Tensor] = None, opts: Optional[Opts] = None,
+                        n_tuples=None) -> torch.Tensor:
+        norb = h1.shape[0]
+        if tuples is not None:
+            self._dev(tuples, torch.int32, "tuples")
+            n_t = tuples.shape[0] if n_tuples is None else n_tuples
+        else:
+            n_t = 1 if n_tuples is None else n_tuples
+        status = self._empty((n_t,), torch.int32)
+        o = (opts or Opts()).to_c()
+        if weights is not None:
+            self._dev(weights, torch.float64, "weights")
+        self._dev(grad_h1, torch.float64, "grad_h1")
+        if grad_eri is not None:
+            self._dev(grad_eri, torch.float64, "grad_eri")
+        _check(lib().casci_rdm_batch(self._h, norb, self._p(self._dev(h1, torch.float64, "h1")),
+                                     self._p(self._dev(eri, torch.float64, "eri")),
+                                     self._p(self._dev(occ, torch.uint8, "occ")), len(ref), _i32_host(ref),
+                                     order, n_t, self._p(tuples), ctypes.byref(o), self._p(weights),
+                                     self._p(grad_h1), self._p(grad_eri), self._p(status)), "casci_rdm_batch")
+        return status
+
+    def mbe_phi_gradient(self, occ, scale: float, grad_h1, grad_eri=None) -> None:
+        _check(lib().mbe_phi_gradient(self._h, grad_h1.shape[0], self._p(self._dev(occ, torch.uint8, "occ")),
+                                      float(scale), self._p(grad_h1), self._p(grad_eri)), "mbe_phi_gradient")
+
+
+def mbe_gradient(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequence[int], orders: Sequence[int],
+                 skip: bool, opts: Optional[Opts] = None, two_body: bool = True, forward=None,
+                 occ_host: Optional[Sequence[int]] = None):
+    """Gradient of the MBE energy with respect to h1 and (pq|rs), on the device.
+
+    E_MBE = E_CAS(R) + sum_S w(S) eps(S) with the adjoint weights of Eq. 2, so
+        dE = dE_Phi + (1 - sum_S w(S)) (dE_CAS(R) - dE_Phi)
+                    + sum_S w(S) (dE_CAS(R u S) - dE_Phi),
+    every term a Hellmann-Feynman density-matrix contraction.  `forward` is the
+    dict of a previous run_mbe (its tuple lists are reused); opts should carry a
+    tight residual tolerance (default here 1e-9).
+    Returns (grad_h1 [norb, norb], grad_eri [norb]*4 or None, forward dict).
+    """
+    opts = opts or Opts(tol=1e-9)
+    if forward is None:
+        forward = run_mbe(ctx, h1, eri, occ, ref, exp, orders, skip, opts, occ_host=occ_host)
+    norb = h1.shape[0]
+    gh = torch.zeros((norb, norb), dtype=torch.float64, device=ctx.device)
+    ge = torch.zeros((norb,) * 4, dtype=torch.float64, device=ctx.device) if two_body else None
+    w = ctx.mbe_weights(forward["tuples"], exp)
+    ctx.mbe_phi_gradient(occ, 1.0, gh, ge)
+    if len(ref) > 0:
+        wsum = float(sum(x.sum() for x in w if x.numel() > 0)) if w else 0.0
+        r_w = torch.tensor([1.0 - wsum], dtype=torch.float64, device=ctx.device)
+        ctx.casci_rdm_batch(h1, eri, occ, ref, 0, None, r_w, gh, ge, opts)
+    for n, tup, wt in zip(orders, forward["tuples"], w):
+        if tup.shape[0] > 0:
+            ctx.casci_rdm_batch(h1, eri, occ, ref, n, tup, wt, gh, ge, opts)
+    return gh, ge, forward
+
+
+class MBEEnergy(torch.autograd.Function):
+    """E_MBE(h1, eri) with a hand-written adjoint (density matrices + Eq. 2 weights)."""
+
+    @staticmethod
+    def forward(fctx, h1, eri, ctx, occ, ref, exp, orders, skip, opts, two_body):
+        out = run_mbe(ctx, h1, eri, occ, ref, exp, orders, skip, opts)
+        fctx.save_for_backward(h1, eri, occ)
+        fctx.cfg = (ctx, ref, exp, orders, skip, opts, two_body, out)
+        return out["e_total"].clone()
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        h1, eri, occ = fctx.saved_tensors
+        ctx, ref, exp, orders, skip, opts, two_body, out = fctx.cfg
+        gh, ge, _ = mbe_gradient(ctx, h1, eri, occ, ref, exp, orders, skip, opts, two_body, forward=out)
+        g = grad_out.reshape(())
+        return g * gh, (g * ge if ge is not None else None), None, None, None, None, None, None, None, None
 
 
 def run_mbe(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequence[int],

@@ -67,6 +67,11 @@ struct BatchArgs {
     int32_t *iters;
     char *scratch;
     size_t slot_bytes;
+    // adjoint (casci_rdm_batch): 0 = energies only, 1 = + 1-RDM, 2 = + 1- and 2-RDM
+    int rdm;
+    const double *weights;
+    double *grad_h1;
+    double *grad_eri;
 };
 
 // ------------------------------------------------------------------ group primitives
@@ -418,6 +423,127 @@ struct PhaseOut {
     int nsig, status;
 };
 
+// ------------------------------------------------------------------ density matrices (adjoint)
+
+// Oriented orbitals of the replacement entry e of string s: E_pq |s> = sign |s'>
+// with p created and q annihilated (p = q for the diagonal entries).
+__device__ inline void entry_orbitals(const Problem &pb, uint32_t s, int32_t e, int &p, int &q)
+{
+    uint32_t sk = pb.str[entry_J(e)];
+    if (sk == s) {
+        p = q = pb.pp[2 * entry_pair(e)];
+    } else {
+        q = __ffs((int)(s & ~sk)) - 1;
+        p = __ffs((int)(sk & ~s)) - 1;
+    }
+}
+
+// Accumulates, for the unit vector c of the (k, k) sector, the spin-free
+//   g1[p n + q]           += <c| E_pq |c>
+//   g2[((p n + q) n + r) n + s] += <c| E_pq E_rs |c>        (g2 may be NULL)
+// with E = E^alpha + E^beta, walking the replacement lists: E_rs |J> = s1 |K>,
+// E_pq |K> = s2 |L> contributes c_L s1 s2 c_J.  Shared- or global-memory atomics.
+template <class G>
+__device__ void rdm_accumulate(const Problem &pb, const double *c, double *g1, double *g2)
+{
+    const int tid = G::rank(), nt = G::size();
+    const int n = pb.n, Ns = pb.Ns, R = pb.R, RS = pb.RS;
+    for (int d = tid; d < pb.N; d += nt) {
+        const double cd = c[d];
+        if (cd == 0.0) continue;
+        const int ja = d / Ns, jb = d - ja * Ns;
+        const uint32_t sa = pb.str[ja], sb = pb.str[jb];
+        const int32_t *ta = pb.tab + ja * RS;
+        const int32_t *tb = pb.tab + jb * RS;
+        for (int x = 0; x < R; ++x) {  // first operator on the alpha string
+            const int e = ta[x], ka = entry_J(e);
+            int p, q;
+            entry_orbitals(pb, sa, e, p, q);
+            atomicAdd(&g1[p * n + q], flip_if(c[ka * Ns + jb], entry_neg(e)) * cd);
+            if (!g2) continue;
+            const double s1cd = flip_if(cd, entry_neg(e));
+            const uint32_t ska = pb.str[ka];
+            const int32_t *tka = pb.tab + ka * RS;
+            for (int x2 = 0; x2 < R; ++x2) {
+                const int e2 = tka[x2];
+                int p2, q2;
+                entry_orbitals(pb, ska, e2, p2, q2);
+                atomicAdd(&g2[((p2 * n + q2) * n + p) * n + q],
+                          flip_if(c[entry_J(e2) * Ns + jb], entry_neg(e2)) * s1cd);
+            }
+            for (int y2 = 0; y2 < R; ++y2) {
+                const int e2 = tb[y2];
+                int p2, q2;
+                entry_orbitals(pb, sb, e2, p2, q2);
+                atomicAdd(&g2[((p2 * n + q2) * n + p) * n + q],
+                          flip_if(c[ka * Ns + entry_J(e2)], entry_neg(e2)) * s1cd);
+            }
+        }
+        for (int y = 0; y < R; ++y) {  // first operator on the beta string
+            const int e = tb[y], kb = entry_J(e);
+            int p, q;
+            entry_orbitals(pb, sb, e, p, q);
+            atomicAdd(&g1[p * n + q], flip_if(c[ja * Ns + kb], entry_neg(e)) * cd);
+            if (!g2) continue;
+            const double s1cd = flip_if(cd, entry_neg(e));
+            const uint32_t skb = pb.str[kb];
+            const int32_t *tkb = pb.tab + kb * RS;
+            for (int x2 = 0; x2 < R; ++x2) {
+                const int e2 = ta[x2];
+                int p2, q2;
+                entry_orbitals(pb, sa, e2, p2, q2);
+                atomicAdd(&g2[((p2 * n + q2) * n + p) * n + q],
+                          flip_if(c[entry_J(e2) * Ns + kb], entry_neg(e2)) * s1cd);
+            }
+            for (int y2 = 0; y2 < R; ++y2) {
+                const int e2 = tkb[y2];
+                int p2, q2;
+                entry_orbitals(pb, skb, e2, p2, q2);
+                atomicAdd(&g2[((p2 * n + q2) * n + p) * n + q],
+                          flip_if(c[ja * Ns + entry_J(e2)], entry_neg(e2)) * s1cd);
+            }
+        }
+    }
+}
+
+// Adds w * (dE_CAS(A)/dtheta - dE_Phi/dtheta) to the gradients from the active
+// density matrices accumulated by rdm_accumulate (Gamma = <E_pq E_rs> - d_qr gamma_ps).
+template <class G>
+__device__ void rdm_flush(const BatchArgs &a, const Problem &pb, const double *g1, const double *g2, double w)
+{
+    const int tid = G::rank(), nt = G::size();
+    const int n = pb.n, norb = a.norb;
+    const int *A = pb.A;
+    for (int e = tid; e < n * n; e += nt) {
+        const int p = e / n, q = e - p * n;
+        const double dg = g1[e] - ((p == q && a.occ[A[p]]) ? 2.0 : 0.0);
+        atomicAdd(&a.grad_h1[A[p] * norb + A[q]], w * dg);
+        if (!g2 || dg == 0.0) continue;
+        const double gc = w * dg;
+        for (int c = 0; c < norb; ++c) {
+            if (!a.occ[c]) continue;
+            bool in_a = false;
+            for (int i = 0; i < n; ++i) in_a |= (A[i] == c);
+            if (in_a) continue;
+            atomicAdd(&a.grad_eri[eri_index(norb, c, c, A[p], A[q])], gc);
+            atomicAdd(&a.grad_eri[eri_index(norb, A[p], A[q], c, c)], gc);
+            atomicAdd(&a.grad_eri[eri_index(norb, c, A[q], A[p], c)], -0.5 * gc);
+            atomicAdd(&a.grad_eri[eri_index(norb, A[p], c, c, A[q])], -0.5 * gc);
+        }
+    }
+    if (!g2) return;
+    for (int e = tid; e < n * n * n * n; e += nt) {
+        const int s = e % n, r = (e / n) % n, q = (e / (n * n)) % n, p = e / (n * n * n);
+        double G = g2[e] - (q == r ? g1[p * n + s] : 0.0);
+        const bool op = a.occ[A[p]], oq = a.occ[A[q]], orr = a.occ[A[r]];
+        double phi = 0.0;
+        if (p == q && r == s && op && orr) phi += (p == r) ? 2.0 : 4.0;
+        if (p == s && q == r && p != q && op && oq) phi -= 2.0;
+        const double v = 0.5 * w * (G - phi);
+        if (v != 0.0) atomicAdd(&a.grad_eri[eri_index(norb, A[p], A[q], A[r], A[s])], v);
+    }
+}
+
 // ------------------------------------------------------------------ warp solver
 
 template <typename T, int DPL>
@@ -619,7 +745,7 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
 
 struct WarpLayout {
     int off_A, off_pp, off_h, off_hp, off_V64, off_V32, off_Hs64, off_Hs32, off_diag, off_c, off_s, off_str,
-        off_tab, bytes;
+        off_tab, off_g1, bytes;
 };
 
 __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
@@ -642,6 +768,7 @@ __host__ __device__ inline WarpLayout warp_layout(int n, int ns, int r, int N)
     L.off_s = o; o = al16(o + 8 * N);
     L.off_str = o; o = al16(o + 4 * ns);
     L.off_tab = o; o = al16(o + 4 * ns * RS);
+    L.off_g1 = o; o = al16(o + 8 * n * n);
     L.bytes = o;
     return L;
 }
@@ -761,6 +888,21 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
             store_result(a, t, e, o64.status, o64.nsig, n32);
         }
         __syncwarp();
+        if (a.rdm) {
+            double *cv = (double *)pb.c;
+            double *g1 = (double *)(ws + L.off_g1);
+#pragma unroll
+            for (int j = 0; j < DPL; ++j) {
+                int d = lane + 32 * j;
+                if (d < pb.N) cv[d] = x64[j];
+            }
+            for (int e = lane; e < n * n; e += 32) g1[e] = 0.0;
+            __syncwarp();
+            rdm_accumulate<WarpGroup>(pb, cv, g1, nullptr);
+            __syncwarp();
+            rdm_flush<WarpGroup>(a, pb, g1, nullptr, a.weights ? a.weights[t] : 1.0);
+            __syncwarp();
+        }
     }
 }
 
@@ -796,10 +938,10 @@ __host__ __device__ inline SlotLayout slot_layout(int ns, int N)
 
 struct BlockSmem {  // dynamic shared memory of the block solver
     int off_A, off_pp, off_h, off_hp, off_V64, off_V32, off_red, off_G, off_A32, off_E32, off_ev, off_y,
-        off_yp, off_r, off_misc, bytes;
+        off_yp, off_r, off_misc, off_g1, off_g2, bytes;
 };
 
-__host__ __device__ inline BlockSmem block_smem(int n)
+__host__ __device__ inline BlockSmem block_smem(int n, bool two_body = false)
 {
     BlockSmem S;
     int P = n * (n + 1) / 2, o = 0;
@@ -818,6 +960,8 @@ __host__ __device__ inline BlockSmem block_smem(int n)
     S.off_yp = o; o = al16(o + 8 * MMAX);
     S.off_r = o; o = al16(o + 8 * MMAX);
     S.off_misc = o; o = al16(o + 8 * 4);
+    S.off_g1 = o; o = al16(o + 8 * n * n);
+    S.off_g2 = o; o = al16(o + (two_body ? 8 * n * n * n * n : 0));
     S.bytes = o;
     return S;
 }
@@ -1170,7 +1314,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
 {
     extern __shared__ __align__(16) char smem[];
     const int n = a.n, P = n * (n + 1) / 2;
-    const BlockSmem S = block_smem(n);
+    const BlockSmem S = block_smem(n, a.rdm == 2);
     int *A = (int *)(smem + S.off_A);
     double *red = (double *)(smem + S.off_red);
     __shared__ unsigned long long s_pos;
@@ -1302,6 +1446,18 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
             store_result(a, t, e, o64.status, o64.nsig, n32);
         }
         __syncthreads();
+        if (a.rdm) {
+            double *g1 = (double *)(smem + S.off_g1);
+            double *g2 = (a.rdm == 2) ? (double *)(smem + S.off_g2) : nullptr;
+            for (int e = threadIdx.x; e < n * n; e += blockDim.x) g1[e] = 0.0;
+            if (g2)
+                for (int e = threadIdx.x; e < n * n * n * n; e += blockDim.x) g2[e] = 0.0;
+            __syncthreads();
+            rdm_accumulate<BlockGroup>(pb, x64, g1, g2);
+            __syncthreads();
+            rdm_flush<BlockGroup>(a, pb, g1, g2, a.weights ? a.weights[t] : 1.0);
+            __syncthreads();
+        }
     }
 }
 
@@ -1420,9 +1576,9 @@ static int launch_warp(mbe_ctx *ctx, const BatchArgs &a, int b, const Bucket &bk
     return tl.done();
 }
 
-static int block_grid(mbe_ctx *ctx, int n, int *grid, size_t *smem)
+static int block_grid(mbe_ctx *ctx, int n, bool two_body, int *grid, size_t *smem)
 {
-    BlockSmem S = block_smem(n);
+    BlockSmem S = block_smem(n, two_body);
     *smem = (size_t)S.bytes;
     MBE_CHECK(*smem <= ctx->smem_optin, MBE_EUNSUPPORTED, "casci_batch: block solver needs %zu B shared memory",
               *smem);
@@ -1438,10 +1594,12 @@ static int block_grid(mbe_ctx *ctx, int n, int *grid, size_t *smem)
 
 using namespace mbe;
 
-extern "C" int casci_batch(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
-                           int n_ref, const int32_t *ref_orbs, double e_ref_corr, int order,
-                           int64_t n_tuples, const int32_t *tuples, const mbe_opts *opts, double *eps_out,
-                           int32_t *status_out, int32_t *iters_out)
+// casci_batch and casci_rdm_batch: rdm = 0 energies only, 1 = + weighted 1-RDM
+// gradients, 2 = + weighted 1- and 2-RDM gradients.
+static int run_casci(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ, int n_ref,
+                     const int32_t *ref_orbs, double e_ref_corr, int order, int64_t n_tuples, const int32_t *tuples,
+                     const mbe_opts *opts, double *eps_out, int32_t *status_out, int32_t *iters_out, int rdm,
+                     const double *weights, double *grad_h1, double *grad_eri)
 {
     MBE_CHECK(ctx != nullptr && h1 != nullptr && eri != nullptr && occ != nullptr, MBE_EINVAL,
               "casci_batch: NULL argument");
@@ -1462,7 +1620,9 @@ extern "C" int casci_batch(mbe_ctx *ctx, int norb, const double *h1, const doubl
     MBE_CHECK(o.tol > 0 && o.tol_switch > 0 && o.max_iter >= 1 && o.fp64_final_iters >= 0, MBE_EINVAL,
               "casci_batch: bad options");
     if (n_tuples == 0) return MBE_OK;
-    MBE_CHECK(eps_out != nullptr && status_out != nullptr, MBE_EINVAL, "casci_batch: NULL output");
+    MBE_CHECK(rdm || (eps_out != nullptr && status_out != nullptr), MBE_EINVAL, "casci_batch: NULL output");
+    MBE_CHECK(!rdm || grad_h1 != nullptr, MBE_EINVAL, "casci_rdm_batch: grad_h1 is NULL");
+    MBE_CHECK(rdm != 2 || n <= 10, MBE_EUNSUPPORTED, "casci_rdm_batch: 2-RDM needs |R| + order <= 10 (got %d)", n);
     MBE_CU(cudaSetDevice(ctx->device));
 
     BatchArgs a;
@@ -1508,7 +1668,7 @@ extern "C" int casci_batch(mbe_ctx *ctx, int norb, const double *h1, const doubl
         a.cls[k].r = st->r;
         int64_t N = st->ns * st->ns;
         int b;
-        if (n <= WARP_MAX_N && N <= WARP_MAX_NDET) {
+        if (n <= WARP_MAX_N && N <= WARP_MAX_NDET && rdm != 2) {
             int di = 0;
             while (DPL_SET[di] * 32 < N) ++di;
             if (warp_bucket_of_dpl[di] < 0) {
@@ -1537,13 +1697,15 @@ extern "C" int casci_batch(mbe_ctx *ctx, int norb, const double *h1, const doubl
     size_t block_smem_bytes = 0;
     size_t slot_bytes = 0;
     if (block_bucket >= 0) {
-        int rc = block_grid(ctx, n, &block_grid_n, &block_smem_bytes);
+        int rc = block_grid(ctx, n, rdm == 2, &block_grid_n, &block_smem_bytes);
         if (rc) return rc;
         slot_bytes = slot_layout(max_block_ns, max_block_ns * max_block_ns).bytes;
     }
 
+    const bool own_out = (eps_out == nullptr || status_out == nullptr);
     size_t bytes = align256((size_t)norb * norb * 8) + align256((size_t)n_tuples * 4) * 2 +
-                   4 * align256((MAX_BUCKETS + 1) * 8) + (size_t)block_grid_n * slot_bytes + 1024;
+                   4 * align256((MAX_BUCKETS + 1) * 8) + (size_t)block_grid_n * slot_bytes +
+                   (own_out ? align256((size_t)n_tuples * 8) + align256((size_t)n_tuples * 4) : 0) + 1024;
     void *ws = nullptr;
     int rc = workspace(ctx, bytes, &ws);
     if (rc) return rc;
@@ -1557,6 +1719,15 @@ extern "C" int casci_batch(mbe_ctx *ctx, int norb, const double *h1, const doubl
     int64_t *bucket_off = bump.take<int64_t>(MAX_BUCKETS + 1);
     char *scratch = nullptr;
     if (block_grid_n > 0) scratch = bump.take<char>((size_t)block_grid_n * slot_bytes);
+    if (own_out) {
+        a.eps = bump.take<double>((size_t)n_tuples);
+        a.status = status_out ? status_out : bump.take<int32_t>((size_t)n_tuples);
+        if (eps_out) a.eps = eps_out;
+    }
+    a.rdm = rdm;
+    a.weights = weights;
+    a.grad_h1 = grad_h1;
+    a.grad_eri = (rdm == 2) ? grad_eri : nullptr;
 
     a.F = F;
     a.perm = perm;
@@ -1598,6 +1769,24 @@ extern "C" int casci_batch(mbe_ctx *ctx, int norb, const double *h1, const doubl
         if (rc) return rc;
     }
     return MBE_OK;
+}
+
+extern "C" int casci_batch(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
+                           int n_ref, const int32_t *ref_orbs, double e_ref_corr, int order,
+                           int64_t n_tuples, const int32_t *tuples, const mbe_opts *opts, double *eps_out,
+                           int32_t *status_out, int32_t *iters_out)
+{
+    return run_casci(ctx, norb, h1, eri, occ, n_ref, ref_orbs, e_ref_corr, order, n_tuples, tuples, opts, eps_out,
+                     status_out, iters_out, 0, nullptr, nullptr, nullptr);
+}
+
+extern "C" int casci_rdm_batch(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
+                               int n_ref, const int32_t *ref_orbs, int order, int64_t n_tuples,
+                               const int32_t *tuples, const mbe_opts *opts, const double *weights, double *grad_h1,
+                               double *grad_eri, int32_t *status_out)
+{
+    return run_casci(ctx, norb, h1, eri, occ, n_ref, ref_orbs, 0.0, order, n_tuples, tuples, opts, nullptr,
+                     status_out, nullptr, grad_eri ? 2 : 1, weights, grad_h1, grad_eri);
 }
 
 // ------------------------------------------------------------------ single active space sigma

@@ -1,5 +1,9 @@
 // a8: increment recursion (Eq. 2); a9: order sums and total (Eq. 1 / Eq. 3);
 // the reference-determinant energy.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
 #include "common.cuh"
 
 namespace mbe {
@@ -104,6 +108,74 @@ __global__ void k_phi_energy(int norb, const double *h1, const double *eri, cons
     if (threadIdx.x == 0) out[0] = part[0];
 }
 
+// ------------------------------------------------------------------ adjoint weights
+
+struct WeightArgs {
+    int order;  // order m of the tuples whose weights this launch computes
+    int n_max;  // highest order present
+    int M;
+    int32_t exp[MBE_MAX_NORB];
+    const int32_t *tuples[MBE_MAX_ORDER];
+    const double *w[MBE_MAX_ORDER];
+    int64_t count[MBE_MAX_ORDER];
+};
+
+// One thread per order-m tuple S: w(S) = 1 - sum over computed proper supersets U
+// of S of w(U).  Supersets S u J, J a j-subset (j = 1 .. n_max - m) of the
+// expansion orbitals outside S, are visited in lexicographic order of J.
+__global__ void k_weights(WeightArgs a, double *w_out)
+{
+    const int m = a.order;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.count[m - 1]) return;
+    int32_t S[MBE_MAX_ORDER], U[MBE_MAX_ORDER], fr[MBE_MAX_NORB];
+    int idx[MBE_MAX_ORDER];
+    for (int i = 0; i < m; ++i) S[i] = a.tuples[m - 1][t * m + i];
+    int nf = 0;
+    for (int i = 0, k = 0; i < a.M; ++i) {
+        while (k < m && S[k] < a.exp[i]) ++k;
+        if (k < m && S[k] == a.exp[i]) continue;
+        fr[nf++] = a.exp[i];
+    }
+    double acc = 0.0;
+    for (int j = 1; j <= a.n_max - m && j <= nf; ++j) {
+        const int mu = m + j;
+        if (a.count[mu - 1] == 0) continue;
+        for (int i = 0; i < j; ++i) idx[i] = i;
+        for (;;) {
+            int x = 0, y = 0, z = 0;  // merge S and fr[idx]
+            while (x < m || y < j) {
+                if (y >= j || (x < m && S[x] < fr[idx[y]])) U[z++] = S[x++];
+                else U[z++] = fr[idx[y++]];
+            }
+            int64_t pos = find_tuple(a.tuples[mu - 1], a.count[mu - 1], mu, U);
+            if (pos >= 0) acc += a.w[mu - 1][pos];
+            int i = j - 1;  // next j-combination of nf
+            while (i >= 0 && idx[i] == nf - j + i) --i;
+            if (i < 0) break;
+            ++idx[i];
+            for (int l = i + 1; l < j; ++l) idx[l] = idx[l - 1] + 1;
+        }
+    }
+    w_out[t] = 1.0 - acc;
+}
+
+// scale * dE_Phi/dtheta, one thread per ordered pair (i, j) of orbitals
+__global__ void k_phi_gradient(int norb, const uint8_t *occ, double scale, double *gh, double *ge)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= norb * norb) return;
+    int i = e / norb, j = e - i * norb;
+    if (!occ[i] || !occ[j]) return;
+    if (i == j) {
+        gh[i * norb + i] += 2.0 * scale;
+        if (ge) ge[(((size_t)i * norb + i) * norb + i) * norb + i] += scale;
+    } else if (ge) {
+        ge[(((size_t)i * norb + i) * norb + j) * norb + j] += 2.0 * scale;
+        ge[(((size_t)i * norb + j) * norb + j) * norb + i] -= scale;
+    }
+}
+
 }  // namespace mbe
 
 using namespace mbe;
@@ -153,6 +225,50 @@ int mbe_increments(mbe_ctx *ctx, int order, int64_t n_tuples, const int32_t *tup
     MBE_CU(cudaSetDevice(ctx->device));
     unsigned g = (unsigned)((n_tuples + 127) / 128);
     k_increments<<<g, 128, 0, ctx->stream>>>(order, n_tuples, tuples, eps, L, inc_out);
+    MBE_CU(cudaGetLastError());
+    ++ctx->launches;
+    return MBE_OK;
+}
+
+int mbe_weights(mbe_ctx *ctx, int n_orders, const int64_t *n_tuples, const int32_t *const *tuples, int n_exp,
+                const int32_t *exp_orbs, double *const *weights)
+{
+    MBE_CHECK(ctx && n_tuples && tuples && weights && (n_exp == 0 || exp_orbs), MBE_EINVAL,
+              "mbe_weights: NULL argument");
+    MBE_CHECK(n_orders >= 1 && n_orders <= MBE_MAX_ORDER, MBE_EINVAL, "mbe_weights: n_orders %d", n_orders);
+    MBE_CHECK(n_exp >= 0 && n_exp <= MBE_MAX_NORB, MBE_EINVAL, "mbe_weights: n_exp %d", n_exp);
+    WeightArgs a;
+    memset(&a, 0, sizeof(a));
+    std::vector<int32_t> ex(exp_orbs, exp_orbs + n_exp);
+    std::sort(ex.begin(), ex.end());
+    for (int i = 0; i < n_exp; ++i) a.exp[i] = ex[i];
+    a.M = n_exp;
+    a.n_max = n_orders;
+    for (int m = 0; m < n_orders; ++m) {
+        MBE_CHECK(n_tuples[m] >= 0 && (n_tuples[m] == 0 || (tuples[m] && weights[m])), MBE_EINVAL,
+                  "mbe_weights: bad list of order %d", m + 1);
+        a.tuples[m] = tuples[m];
+        a.w[m] = weights[m];
+        a.count[m] = n_tuples[m];
+    }
+    MBE_CU(cudaSetDevice(ctx->device));
+    for (int m = n_orders; m >= 1; --m) {
+        if (a.count[m - 1] == 0) continue;
+        a.order = m;
+        unsigned g = (unsigned)((a.count[m - 1] + 127) / 128);
+        k_weights<<<g, 128, 0, ctx->stream>>>(a, weights[m - 1]);
+        MBE_CU(cudaGetLastError());
+        ++ctx->launches;
+    }
+    return MBE_OK;
+}
+
+int mbe_phi_gradient(mbe_ctx *ctx, int norb, const uint8_t *occ, double scale, double *grad_h1, double *grad_eri)
+{
+    MBE_CHECK(ctx && occ && grad_h1, MBE_EINVAL, "mbe_phi_gradient: NULL argument");
+    MBE_CHECK(norb >= 1 && norb <= MBE_MAX_NORB, MBE_EINVAL, "mbe_phi_gradient: norb %d", norb);
+    MBE_CU(cudaSetDevice(ctx->device));
+    k_phi_gradient<<<(norb * norb + 127) / 128, 128, 0, ctx->stream>>>(norb, occ, scale, grad_h1, grad_eri);
     MBE_CU(cudaGetLastError());
     ++ctx->launches;
     return MBE_OK;

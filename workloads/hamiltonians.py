@@ -217,7 +217,7 @@ def block_decoupled_system(n1: int, nocc1: int, n2: int, nocc2: int, seed: int,
     return h1, eri, occ, block
 
 
-WORKLOAD_NAMES = ("hubbard8", "hubbard22", "molecule40", "hubbard46")
+WORKLOAD_NAMES = ("hubbard8", "hubbard22", "molecule40", "hubbard46", "molecule20")
 
 
 def workload(name: str) -> Workload:
@@ -232,6 +232,8 @@ def workload(name: str) -> Workload:
                  over the other 34 orbitals to order 4.
     hubbard46  : L=46 ring, t=1, U=4, half filling, empty reference, orders 1-4,
                  with the same skip rule as hubbard22.
+    molecule20 : molecule40 truncated to orbitals 0..19 (same occupation and
+                 reference space), orders 1-4; the adjoint workload.
     """
     if name == "hubbard8":
         h1, eri, occ, _ = hubbard_ring_momentum(8, 1.0, 2.0)
@@ -252,4 +254,14 @@ def workload(name: str) -> Workload:
         return Workload(name, h1, eri, occ, ref, exp, list(range(1, 5)), False,
                         "synthetic 40-orbital molecule, (6e,6o) reference, orders 1-4",
                         dict(seed=1910))
+    if name == "molecule20":
+        h1, eri, occ = synthetic_molecule(1910)
+        keep = list(range(20))
+        h1 = np.ascontiguousarray(h1[np.ix_(keep, keep)])
+        eri = np.ascontiguousarray(eri[np.ix_(keep, keep, keep, keep)])
+        ref = list(range(5, 11))
+        exp = [p for p in range(20) if p not in ref]
+        return Workload(name, h1, eri, occ[:20].copy(), ref, exp, list(range(1, 5)), False,
+                        "synthetic molecule truncated to its first 20 orbitals, (6e,6o) reference, "
+                        "orders 1-4", dict(seed=1910))
     raise KeyError(name)
