@@ -438,6 +438,65 @@ def run_ncu_case(args):
     ctx.close()
 
 
+def run_large(args):
+    """Single large CASCI on the synthetic 40-orbital molecule: one float64 and one
+    float32 sigma at (12e,12o), (14e,14o), (16e,16o), timed with CUDA events inside
+    the library, and a mixed-precision Davidson solve at (12e,12o)."""
+    import numpy as np
+    import torch
+
+    import paper_1910_03527_gb300 as eng
+    from workloads import synthetic_molecule
+
+    eng.build()
+    dev = torch.device("cuda", 0)
+    ctx = eng.Context(0)
+    h1, eri, occ = synthetic_molecule(1910)
+    th1, teri, tocc = (torch.tensor(x, device=dev) for x in (h1, eri, occ))
+    actives = {12: list(range(2, 14)), 14: list(range(1, 15)), 16: list(range(0, 16))}
+    out = {"metric": "single-CASCI sigma throughput (determinants/s) and fraction of ALU peak",
+           "workload": "synthetic 40-orbital molecule (seed 1910), (12e,12o) {2..13}, (14e,14o) {1..14}, "
+                       "(16e,16o) {0..15}", "sigma": {}}
+    for n in args.large_sizes:
+        A = actives[n]
+        k = int(sum(int(occ[p]) for p in A))
+        ns = math.comb(n, k)
+        N = ns * ns
+        r = k * (n - k + 1)
+        conn = 1 + k * (n - k) + math.comb(k, 2) * math.comb(n - k, 2)
+        flops = N * 2 * (2 * conn + r * r)
+        c = torch.randn(N, dtype=torch.float64, device=dev)
+        entry = {"determinants": N}
+        for prec in ("fp64", "mixed"):
+            ctx.casci_sigma_large(th1, teri, tocc, A, c, prec)  # warm-up (and set-up)
+            torch.cuda.synchronize()
+            ctx.take_timings()
+            ctx.set_timing(True)
+            for _ in range(args.steps):
+                ctx.casci_sigma_large(th1, teri, tocc, A, c, prec)
+            recs = ctx.take_timings()
+            ctx.set_timing(False)
+            ms = statistics.median([x[3] for x in recs if x[1] == 2])
+            peak = PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS
+            entry[prec] = {"ms": ms, "dets_per_s": N / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12,
+                           "alu_frac": flops / (ms / 1e3) / 1e12 / peak,
+                           "peak_tflops": peak, "flop_per_sigma": flops}
+        out["sigma"][f"{n}o"] = entry
+        del c
+        torch.cuda.empty_cache()
+    solves = {}
+    for prec in ("mixed", "fp64"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ctx.casci_solve(th1, teri, tocc, actives[12], eng.Opts(precision=prec, tol=1e-8))
+        torch.cuda.synchronize()
+        solves[prec] = dict(res, seconds=time.perf_counter() - t0)
+    out["solve_12o"] = solves
+    out["solve_12o"]["abs_diff_lambda"] = abs(solves["mixed"]["lam"] - solves["fp64"]["lam"])
+    print(json.dumps(out))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -451,7 +510,13 @@ def main():
     ap.add_argument("--ncu-case", choices=["fp64", "mixed"], default=None,
                     help="run only casci_batch on one order of the workload (for ncu captures)")
     ap.add_argument("--ncu-order", type=int, default=6)
+    ap.add_argument("--large", action="store_true",
+                    help="single large CASCI: sigma throughput at 12/14/16 orbitals and a 12-orbital solve")
+    ap.add_argument("--large-sizes", type=int, nargs="+", default=[12, 14, 16])
     args = ap.parse_args()
+    if args.large:
+        run_large(args)
+        return
     if args.oracle_sample is not None:
         print(json.dumps(oracle_sample(args.oracle_sample)))
         return

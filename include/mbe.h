@@ -113,9 +113,9 @@ int mbe_ctx_launches(const mbe_ctx *ctx, int64_t *count);
    clears them.  solver: 0 = one tuple per warp (dpl = determinants per lane),
    1 = one tuple per thread block.  Not for use during stream capture. */
 typedef struct mbe_timing {
-    int order;  /* tuple order of the casci_batch call   */
-    int solver; /* 0 warp solver, 1 block solver          */
-    int dpl;    /* determinants per lane (warp solver)    */
+    int order;  /* tuple order of the casci_batch call (n_cas for solver 2) */
+    int solver; /* 0 warp solver, 1 block solver, 2 large-CAS sigma         */
+    int dpl;    /* determinants per lane (warp solver); 64 or 32 (solver 2: precision) */
     float ms;   /* elapsed time of the launch             */
 } mbe_timing;
 int mbe_ctx_set_timing(mbe_ctx *ctx, int enable);
@@ -305,6 +305,41 @@ int casci_rdm_batch(mbe_ctx *ctx, int norb, const double *h1, const double *eri,
  */
 int mbe_phi_gradient(mbe_ctx *ctx, int norb, const uint8_t *occ, double scale, double *grad_h1,
                      double *grad_eri);
+
+/* ------------------------------------------------------------------ a5-a6: one large CAS */
+
+#define MBE_MAX_LARGE_CAS 16 /* orbitals of casci_sigma_large / casci_solve */
+
+/*
+ * sigma = H_A c for one large active space (the tuple CASCI sigma of a5 at the
+ * sizes of a single big CASCI: up to 16 orbitals, (16e,16o) = 165,636,900
+ * determinants), spread over the whole GPU.  Same operator, determinant order
+ * and layouts as casci_sigma; the same-spin part uses a compressed (CSR) copy
+ * of the one-spin Hamiltonian.
+ *   precision   MBE_PREC_FP64: float64 arithmetic; MBE_PREC_MIXED: float32
+ *               arithmetic on a float32 copy of c (result written as float64)
+ *   c, sigma    device [N], N = C(n_cas, k)^2, k = |O n A|; diag device or NULL
+ * Synchronous set-up (occupations read back), then asynchronous on the stream.
+ * Errors: MBE_EINVAL, MBE_EUNSUPPORTED (n_cas > 16), MBE_ENOMEM, MBE_ECUDA.
+ */
+int casci_sigma_large(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
+                      int n_cas, const int32_t *cas_orbs, int precision, const double *c, double *sigma,
+                      double *diag);
+
+/*
+ * Lowest eigenpair of one large active space (a6 for a single big CASCI): the
+ * Davidson of casci_batch (12-vector basis, thick restart on the two lowest
+ * Ritz vectors, float32 then float64 phase in mixed mode) with every vector
+ * operation in grid-wide kernels and the projected eigenproblem solved by one
+ * warp on the device.  Synchronous: the host reads one residual norm per
+ * iteration.
+ *   result [3]  host out: lambda, eps = lambda - <Phi_A|H_A|Phi_A>, residual norm
+ *   info [3]    host out: status (MBE_STATUS_*), float64 sigma products, float32 ones
+ *   cvec [N]    device out (the unit Ritz vector) or NULL
+ * Errors: as casci_sigma_large.
+ */
+int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ, int n_cas,
+                const int32_t *cas_orbs, const mbe_opts *opts, double *result, int32_t *info, double *cvec);
 
 /* ------------------------------------------------------------------ a8-a9: Eqs. 2, 1 */
 

@@ -30,7 +30,7 @@ EXPORTS = ("mbe_default_opts", "mbe_ctx_create", "mbe_ctx_set_stream", "mbe_ctx_
            "mbe_last_error", "mbe_ctx_sync", "mbe_ctx_launches", "mbe_ctx_set_timing",
            "mbe_ctx_timings", "mbe_tuples", "mbe_string_table", "mbe_phi_energy",
            "casci_batch", "casci_sigma", "casci_sigma_noalloc", "mbe_increments", "mbe_total",
-           "mbe_weights", "casci_rdm_batch", "mbe_phi_gradient")
+           "mbe_weights", "casci_rdm_batch", "mbe_phi_gradient", "casci_sigma_large", "casci_solve")
 
 
 class MbeOpts(ctypes.Structure):
@@ -102,6 +102,10 @@ def lib() -> ctypes.CDLL:
     L.casci_rdm_batch.argtypes = [P, i32, P, P, P, i32, P, i32, i64, P, ctypes.POINTER(MbeOpts), P, P, P, P]
     L.mbe_phi_gradient.restype = i32
     L.mbe_phi_gradient.argtypes = [P, i32, P, dbl, P, P]
+    L.casci_sigma_large.restype = i32
+    L.casci_sigma_large.argtypes = [P, i32, P, P, P, i32, P, i32, P, P, P]
+    L.casci_solve.restype = i32
+    L.casci_solve.argtypes = [P, i32, P, P, P, i32, P, ctypes.POINTER(MbeOpts), P, P, P]
     return L
 
 
@@ -340,6 +344,40 @@ class Context:
     def mbe_phi_gradient(self, occ, scale: float, grad_h1, grad_eri=None) -> None:
         _check(lib().mbe_phi_gradient(self._h, grad_h1.shape[0], self._p(self._dev(occ, torch.uint8, "occ")),
                                       float(scale), self._p(grad_h1), self._p(grad_eri)), "mbe_phi_gradient")
+
+    def casci_sigma_large(self, h1, eri, occ, cas: Sequence[int], c: torch.Tensor, precision: str = "fp64",
+                          want_diag: bool = False):
+        norb = h1.shape[0]
+        self._dev(c, torch.float64, "c")
+        sigma = torch.empty_like(c)
+        diag = torch.empty_like(c) if want_diag else None
+        prec = {"fp64": MBE_PREC_FP64, "mixed": MBE_PREC_MIXED}[precision]
+        _check(lib().casci_sigma_large(self._h, norb, self._p(self._dev(h1, torch.float64, "h1")),
+                                       self._p(self._dev(eri, torch.float64, "eri")),
+                                       self._p(self._dev(occ, torch.uint8, "occ")), len(cas), _i32_host(cas),
+                                       prec, self._p(c), self._p(sigma), self._p(diag)), "casci_sigma_large")
+        return sigma, diag
+
+    def casci_solve(self, h1, eri, occ, cas: Sequence[int], opts: Optional[Opts] = None, want_vector=False):
+        """Lowest eigenpair of one large active space: dict(lambda, eps, rnorm, status, n64, n32[, c])."""
+        norb = h1.shape[0]
+        res = (ctypes.c_double * 3)()
+        info = (ctypes.c_int32 * 3)()
+        o = (opts or Opts()).to_c()
+        cvec = None
+        if want_vector:
+            import math
+            occ_h = occ.cpu().tolist()
+            k = sum(int(occ_h[p]) for p in cas)
+            cvec = self._empty((math.comb(len(cas), k) ** 2,), torch.float64)
+        _check(lib().casci_solve(self._h, norb, self._p(self._dev(h1, torch.float64, "h1")),
+                                 self._p(self._dev(eri, torch.float64, "eri")),
+                                 self._p(self._dev(occ, torch.uint8, "occ")), len(cas), _i32_host(cas),
+                                 ctypes.byref(o), res, info, self._p(cvec)), "casci_solve")
+        out = dict(lam=res[0], eps=res[1], rnorm=res[2], status=info[0], n64=info[1], n32=info[2])
+        if cvec is not None:
+            out["c"] = cvec
+        return out
 
 
 def mbe_gradient(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequence[int], orders: Sequence[int],

@@ -25,6 +25,7 @@
 // the vectors and Hs in a per-block slot of the context workspace.  Both are
 // persistent kernels that pull tuples from an atomic counter per bucket.
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -998,8 +999,8 @@ __device__ inline void block_sum_n(T (&v)[KRED], int k, T *red)
 // r = G y - theta y,  theta = y.G y, make the lowest pair float64-accurate.
 // Output: y[0..m) (shared, float64, unit norm) and misc[0] = theta.
 template <bool REFINE>
-__device__ void small_eig_warp(const double *G, int m, float *A, float *E, float *ev, double *y, double *r,
-                               double *misc)
+__device__ void small_eig_warp(const double *G, int m, float *A, float *E, float *ev, double *y, double *y2,
+                               double *r, double *misc)
 {
     const int lane = threadIdx.x & 31;
     const double shift = G[0];
@@ -1067,9 +1068,22 @@ __device__ void small_eig_warp(const double *G, int m, float *A, float *E, float
             bi = oi;
         }
     }
+    // second-lowest eigenvalue (its eigenvector seeds the thick restart)
+    float best2 = (lane < m && lane != bi) ? A[lane * MMAX + lane] : 3.0e38f;
+    int b2 = (lane < m && lane != bi) ? lane : 0x7fffffff;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float ov = __shfl_xor_sync(FULL, best2, o);
+        int oi = __shfl_xor_sync(FULL, b2, o);
+        if (ov < best2 || (ov == best2 && oi < b2)) {
+            best2 = ov;
+            b2 = oi;
+        }
+    }
     if (lane < m) {
         ev[lane] = A[lane * MMAX + lane];
         y[lane] = (double)E[lane * MMAX + bi];
+        y2[lane] = (b2 < m) ? (double)E[lane * MMAX + b2] : 0.0;
     }
     __syncwarp();
     double theta = shift + (double)best;
@@ -1123,7 +1137,7 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
     float *E32 = (float *)(smem + S.off_E32);
     float *ev = (float *)(smem + S.off_ev);
     double *ys = (double *)(smem + S.off_y);
-    double *yps = (double *)(smem + S.off_yp);
+    double *y2s = (double *)(smem + S.off_yp);
     double *rs = (double *)(smem + S.off_r);
     double *misc = (double *)(smem + S.off_misc);
     PhaseOut o;
@@ -1146,18 +1160,18 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
     if (tid == 0) G[0] = (double)v[0];
     __syncthreads();
     int m = 1;
-    bool have_prev = false;
     double theta = 0.0;
     T rn = 0;
     T best = (T)3e38;
     int stall = 0;
     for (int it = 0;; ++it) {
-        if (tid < 32) small_eig_warp<sizeof(T) == 8>(G, m, A32, E32, ev, ys, rs, misc);
+        if (tid < 32) small_eig_warp<sizeof(T) == 8>(G, m, A32, E32, ev, ys, y2s, rs, misc);
         __syncthreads();
         theta = misc[0];
         const T th = (T)theta;
         T *tdst = (m < MMAX) ? V + (size_t)m * ld : tx;
         v[0] = 0;
+        v[1] = 0;
         for (int d = tid; d < N; d += nt) {
             T xs = 0, hs = 0;
             for (int i = 0; i < m; ++i) {
@@ -1171,10 +1185,13 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
             v[0] += r * r;
             T den = (T)pb.diag[d] - th;
             if (fabs(den) < (T)1e-4) den = den >= (T)0 ? (T)1e-4 : (T)-1e-4;
-            tdst[d] = r / den;
+            const T td = r / den;
+            tdst[d] = td;
+            v[1] += td * td;
         }
-        block_sum_n<T>(v, 1, red);
+        block_sum_n<T>(v, 2, red);
         rn = sqrt(v[0]);
+        const T t0n = sqrt(v[1]);
         if (!isfinite(rn) || !isfinite(theta)) {
             o.status = MBE_STATUS_NONFINITE;
             break;
@@ -1193,45 +1210,42 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
             }
         }
         if (m == MMAX) {
-            // Thick restart: basis {x, previous Ritz vector}, orthonormalised twice.
+            // Thick restart on the two lowest Ritz vectors of the current basis
+            // (orthogonal by construction, so W stays consistent with H V).
             for (int d = tid; d < N; d += nt) {
-                T xp = 0, hxp = 0;
-                if (have_prev) {
-                    for (int i = 0; i < MMAX; ++i) {
-                        T yi = (T)yps[i];
-                        xp += yi * V[(size_t)i * ld + d];
-                        hxp += yi * W[(size_t)i * ld + d];
-                    }
+                T x2 = 0, hx2 = 0;
+                for (int i = 0; i < MMAX; ++i) {
+                    T yi = (T)y2s[i];
+                    x2 += yi * V[(size_t)i * ld + d];
+                    hx2 += yi * W[(size_t)i * ld + d];
                 }
                 V[d] = x[d];
                 W[d] = hx[d];
-                V[ld + d] = xp;
-                W[ld + d] = hxp;
+                V[ld + d] = x2;
+                W[ld + d] = hx2;
             }
             __syncthreads();
-            int mnew = 1;
-            if (have_prev) {
-                for (int pass = 0; pass < 2; ++pass) {
-                    v[0] = 0;
-                    for (int d = tid; d < N; d += nt) v[0] += V[d] * V[ld + d];
-                    block_sum_n<T>(v, 1, red);
-                    for (int d = tid; d < N; d += nt) {
-                        V[ld + d] -= v[0] * V[d];
-                        W[ld + d] -= v[0] * W[d];
-                    }
-                }
+            for (int pass = 0; pass < 2; ++pass) {
                 v[0] = 0;
-                for (int d = tid; d < N; d += nt) v[0] += V[ld + d] * V[ld + d];
+                for (int d = tid; d < N; d += nt) v[0] += V[d] * V[ld + d];
                 block_sum_n<T>(v, 1, red);
-                T nn = sqrt(v[0]);
-                if (nn > tiny_norm<T>()) {
-                    T inv = (T)1 / nn;
-                    for (int d = tid; d < N; d += nt) {
-                        V[ld + d] *= inv;
-                        W[ld + d] *= inv;
-                    }
-                    mnew = 2;
+                for (int d = tid; d < N; d += nt) {
+                    V[ld + d] -= v[0] * V[d];
+                    W[ld + d] -= v[0] * W[d];
                 }
+            }
+            v[0] = 0;
+            for (int d = tid; d < N; d += nt) v[0] += V[ld + d] * V[ld + d];
+            block_sum_n<T>(v, 1, red);
+            int mnew = 1;
+            T nn = sqrt(v[0]);
+            if (nn > (T)0.5) {
+                T inv = (T)1 / nn;
+                for (int d = tid; d < N; d += nt) {
+                    V[ld + d] *= inv;
+                    W[ld + d] *= inv;
+                }
+                mnew = 2;
             }
             v[0] = v[1] = v[2] = 0;
             for (int d = tid; d < N; d += nt) {
@@ -1250,11 +1264,6 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
                 }
             }
             m = mnew;
-            have_prev = false;
-        } else {
-            // ys is rewritten by the next eigensolve only after the barriers below
-            if (tid < MMAX) yps[tid] = (tid < m) ? ys[tid] : 0.0;
-            have_prev = true;
         }
         // Correction: orthogonalise against V[0..m) twice, into V[m].
         T *tv = V + (size_t)m * ld;
@@ -1281,7 +1290,8 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
         for (int d = tid; d < N; d += nt) v[0] += tv[d] * tv[d];
         block_sum_n<T>(v, 1, red);
         T tn = sqrt(v[0]);
-        if (!(tn > tiny_norm<T>())) {
+        if (!(tn > (T)1e-12 * t0n) || !(tn > (T)0)) {
+            // The correction lies in the current basis: nothing left to add.
             if (!steer && rn > (T)tol) o.status = MBE_STATUS_MAXITER;
             break;
         }
@@ -2021,4 +2031,836 @@ extern "C" int casci_sigma_noalloc(int device, void *cuda_stream, int norb, cons
     }
     if (prev != device) cudaSetDevice(prev);
     return rc;
+}
+
+// ------------------------------------------------------------------ single large active space
+//
+// One CASCI over a large active space (up to 16 orbitals, 165.6M determinants
+// at (16e,16o)), spread over the whole GPU:
+//   * set-up: h_eff, packed V, h' (one block); the one-spin Hamiltonian Hs built
+//     column-parallel over the grid as a dense Ns x Ns matrix, then compressed to
+//     CSR (each row holds the strings connected by at most a double replacement);
+//   * sigma: one thread per determinant; Hs C and C Hs^T through the CSR rows
+//     (the first one coalesced over the beta index), the opposite-spin term as the
+//     direct double loop over replacement lists with V staged in shared memory;
+//     float32 or float64 arithmetic;
+//   * Davidson: the tuple solvers' algorithm (MLARGE-vector basis, thick restart
+//     on the two lowest Ritz vectors, float32 phase then float64 phase) with its
+//     vector algebra in grid-wide kernels, the projected eigenproblem in one
+//     warp on the device, and the host reading back one residual norm per
+//     iteration to decide convergence.
+
+namespace mbe {
+
+constexpr int MLARGE = 12;      // Davidson basis of the large solver (<= MMAX)
+constexpr int LRED = MLARGE + 2;  // values per grid reduction
+constexpr int LARGE_THREADS = 256;
+constexpr int SIGMA_THREADS = 512;
+
+struct LargeCas {
+    int n, P, k, Ns, R;
+    int64_t N;
+    const uint32_t *str;
+    const int32_t *tab;
+    double *V;      // [P*P]
+    float *V32;     // [P*P]
+    double *hp;     // [P]
+    short *pp;      // [2P]
+    double *Hd;     // dense Hs [Ns*Ns] (set-up only)
+    int64_t *roff;  // CSR [Ns+1]
+    int32_t *col;   // CSR [nnz]
+    double *val;    // CSR [nnz]
+    float *val32;   // CSR [nnz]
+    double *diag;   // [N]
+    int64_t nnz;
+};
+
+__global__ void k_scan_counts(const int32_t *counts, int64_t nblocks, int64_t *offsets);
+
+struct LargeSetupArgs {
+    int norb;
+    const double *eri;
+    const double *F;
+    const uint8_t *occ;
+    int A[MBE_MAX_STRING_ORB];
+};
+
+// One block: pair table, h_eff, V over packed pairs (float64 and float32), h'.
+__global__ void __launch_bounds__(CTA_THREADS) k_large_setup(LargeSetupArgs a, LargeCas L)
+{
+    __shared__ int A[MBE_MAX_STRING_ORB];
+    __shared__ double h[MBE_MAX_STRING_ORB * MBE_MAX_STRING_ORB];
+    const int n = L.n, P = L.P, norb = a.norb;
+    if (threadIdx.x < n) A[threadIdx.x] = a.A[threadIdx.x];
+    for (int e = threadIdx.x; e < P; e += blockDim.x) {
+        int p = 0;
+        while ((p + 1) * (p + 2) / 2 <= e) ++p;
+        L.pp[2 * e] = (short)p;
+        L.pp[2 * e + 1] = (short)(e - p * (p + 1) / 2);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int x = e / n, y = e - x * n;
+        int gp = A[x], gq = A[y];
+        double v = a.F[gp * norb + gq];
+        for (int c = 0; c < n; ++c) {
+            int gi = A[c];
+            if (a.occ[gi])
+                v -= 2.0 * a.eri[eri_index(norb, gp, gq, gi, gi)] - a.eri[eri_index(norb, gp, gi, gi, gq)];
+        }
+        h[e] = v;
+    }
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+        int x = e / P, y = e - x * P;
+        int p = L.pp[2 * x], q = L.pp[2 * x + 1], r = L.pp[2 * y], s = L.pp[2 * y + 1];
+        double v = a.eri[eri_index(norb, A[p], A[q], A[r], A[s])];
+        L.V[e] = v;
+        L.V32[e] = (float)v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < P; e += blockDim.x) {
+        int p = L.pp[2 * e], q = L.pp[2 * e + 1];
+        double v = h[p * n + q];
+        for (int r = 0; r < n; ++r) v -= 0.5 * L.V[pair_index(p, r) * P + pair_index(r, q)];
+        L.hp[e] = v;
+    }
+}
+
+// Dense Hs, one column J per thread (same recursion as the tuple set-up).
+__global__ void k_large_hs_cols(LargeCas L)
+{
+    int J = blockIdx.x * blockDim.x + threadIdx.x;
+    if (J >= L.Ns) return;
+    const int Ns = L.Ns, R = L.R, P = L.P;
+    for (int I = 0; I < Ns; ++I) L.Hd[(size_t)I * Ns + J] = 0.0;
+    const int32_t *tj = L.tab + (size_t)J * R;
+    for (int b = 0; b < R; ++b) {
+        int eb = tj[b];
+        int K = entry_J(eb), rs = entry_pair(eb);
+        double sb = entry_neg(eb) ? -1.0 : 1.0;
+        L.Hd[(size_t)K * Ns + J] += sb * L.hp[rs];
+        const int32_t *tk = L.tab + (size_t)K * R;
+        for (int q = 0; q < R; ++q) {
+            int ea = tk[q];
+            double sa = entry_neg(ea) ? -1.0 : 1.0;
+            L.Hd[(size_t)entry_J(ea) * Ns + J] += 0.5 * sa * sb * L.V[entry_pair(ea) * P + rs];
+        }
+    }
+}
+
+// Non-zeros per row (one warp per row), for the CSR offsets.
+__global__ void k_large_hs_count(LargeCas L, int32_t *cnt)
+{
+    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= L.Ns) return;
+    const double *hr = L.Hd + (size_t)row * L.Ns;
+    int c = 0;
+    for (int base = 0; base < L.Ns; base += 32) {
+        int j = base + lane;
+        bool nz = j < L.Ns && hr[j] != 0.0;
+        c += __popc(__ballot_sync(FULL, nz));
+    }
+    if (lane == 0) cnt[row] = c;
+}
+
+__global__ void k_large_hs_fill(LargeCas L, const int64_t *off)
+{
+    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= L.Ns) return;
+    const double *hr = L.Hd + (size_t)row * L.Ns;
+    int64_t pos = off[row];
+    if (lane == 0) L.roff[row] = pos;
+    if (row == L.Ns - 1 && lane == 0) L.roff[L.Ns] = off[L.Ns];
+    for (int base = 0; base < L.Ns; base += 32) {
+        int j = base + lane;
+        double v = (j < L.Ns) ? hr[j] : 0.0;
+        unsigned m = __ballot_sync(FULL, v != 0.0);
+        if (v != 0.0) {
+            int64_t at = pos + __popc(m & ((1u << lane) - 1u));
+            L.col[at] = j;
+            L.val[at] = v;
+            L.val32[at] = (float)v;
+        }
+        pos += __popc(m);
+    }
+}
+
+__global__ void k_large_diag(LargeCas L)
+{
+    const int Ns = L.Ns, P = L.P;
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < L.N; d += (int64_t)gridDim.x * blockDim.x) {
+        int ia = (int)(d / Ns), ib = (int)(d - (int64_t)ia * Ns);
+        double v = L.Hd[(size_t)ia * Ns + ia] + L.Hd[(size_t)ib * Ns + ib];
+        uint32_t sa = L.str[ia];
+        while (sa) {
+            int p = __ffs((int)sa) - 1;
+            sa &= sa - 1;
+            uint32_t sb = L.str[ib];
+            while (sb) {
+                int q = __ffs((int)sb) - 1;
+                sb &= sb - 1;
+                v += L.V[pair_index(p, p) * P + pair_index(q, q)];
+            }
+        }
+        L.diag[d] = v;
+    }
+}
+
+// sigma = H c over the whole determinant space; T is the arithmetic type, c is
+// read as T (a float copy in the float32 phase), sigma is written as float64.
+template <typename T>
+__global__ void __launch_bounds__(SIGMA_THREADS) k_large_sigma(LargeCas L, const T *__restrict__ c,
+                                                                double *__restrict__ sigma)
+{
+    extern __shared__ __align__(16) char smem[];
+    T *Vs = (T *)smem;
+    const int P = L.P, Ns = L.Ns, R = L.R;
+    const T *Vg = sizeof(T) == 8 ? (const T *)L.V : (const T *)L.V32;
+    const T *val = sizeof(T) == 8 ? (const T *)L.val : (const T *)L.val32;
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) Vs[e] = Vg[e];
+    __syncthreads();
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < L.N; d += (int64_t)gridDim.x * blockDim.x) {
+        const int ia = (int)(d / Ns), ib = (int)(d - (int64_t)ia * Ns);
+        T acc0 = 0, acc1 = 0;
+        for (int64_t e = L.roff[ia]; e < L.roff[ia + 1]; ++e)
+            acc0 = fma(val[e], c[(int64_t)L.col[e] * Ns + ib], acc0);
+        const T *crow = c + (int64_t)ia * Ns;
+        for (int64_t e = L.roff[ib]; e < L.roff[ib + 1]; ++e) acc1 = fma(val[e], crow[L.col[e]], acc1);
+        const int32_t *ta = L.tab + (size_t)ia * R;
+        const int32_t *tb = L.tab + (size_t)ib * R;
+        for (int x = 0; x < R; ++x) {
+            const int ea = ta[x];
+            const T *vrow = Vs + entry_pair(ea) * P;
+            const T *cr = c + (int64_t)entry_J(ea) * Ns;
+            T s0 = 0, s1 = 0;
+            int y = 0;
+            for (; y + 1 < R; y += 2) {
+                const int e0 = tb[y], e1 = tb[y + 1];
+                s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), cr[entry_J(e0)], s0);
+                s1 = fma(flip_if(vrow[entry_pair(e1)], entry_neg(e1)), cr[entry_J(e1)], s1);
+            }
+            if (y < R) {
+                const int e0 = tb[y];
+                s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), cr[entry_J(e0)], s0);
+            }
+            const T s = s0 + s1;
+            if (x & 1) acc1 += flip_if(s, entry_neg(ea)); else acc0 += flip_if(s, entry_neg(ea));
+        }
+        sigma[d] = (double)(acc0 + acc1);
+    }
+}
+
+// ---- grid-wide vector algebra of the large Davidson (all float64)
+
+// partial[b*K + i] = block b's share of sum_d A_i[d] * u[d], i < K; A_i = A + i*ld.
+__global__ void __launch_bounds__(LARGE_THREADS) k_multidot(const double *A, size_t ld, int K, const double *u,
+                                                            int64_t N, double *partial)
+{
+    __shared__ double red[32 * LRED];
+    double v[LRED];
+#pragma unroll
+    for (int i = 0; i < LRED; ++i) v[i] = 0.0;
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < N; d += (int64_t)gridDim.x * blockDim.x) {
+        const double ud = u[d];
+#pragma unroll
+        for (int i = 0; i < LRED; ++i)
+            if (i < K) v[i] += A[i * ld + d] * ud;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < LRED; ++i)
+        if (i < K) v[i] = warp_sum(v[i]);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < LRED; ++i)
+            if (i < K) red[w * LRED + i] = v[i];
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int j = 0; j < nw; ++j) s += red[j * LRED + threadIdx.x];
+        partial[(size_t)blockIdx.x * K + threadIdx.x] = s;
+    }
+}
+
+// out[i] = sum over blocks of partial (fixed order); one warp per value.
+__global__ void k_multidot_final(const double *partial, int nblocks, int K, double *out)
+{
+    const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (i >= K) return;
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += partial[(size_t)b * K + i];
+    s = warp_sum(s);
+    if (lane == 0) out[i] = s;
+}
+
+// x = V y, hx = W y, r = hx - theta x, t = r / clamp(diag - theta); partial sums of
+// |r|^2 and |t|^2 (two values per block).
+__global__ void __launch_bounds__(LARGE_THREADS) k_ritz(const double *V, const double *W, size_t ld, int m,
+                                                        const double *ys, const double *misc, const double *diag,
+                                                        int64_t N, double *x, double *hx, double *t,
+                                                        double *partial)
+{
+    __shared__ double red[64];
+    const double th = misc[0];
+    double y[MLARGE];
+#pragma unroll
+    for (int i = 0; i < MLARGE; ++i) y[i] = (i < m) ? ys[i] : 0.0;
+    double rr = 0.0, tt = 0.0;
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < N; d += (int64_t)gridDim.x * blockDim.x) {
+        double xs = 0.0, hs = 0.0;
+#pragma unroll
+        for (int i = 0; i < MLARGE; ++i)
+            if (i < m) {
+                xs += y[i] * V[i * ld + d];
+                hs += y[i] * W[i * ld + d];
+            }
+        x[d] = xs;
+        hx[d] = hs;
+        double r = hs - th * xs;
+        double den = diag[d] - th;
+        if (fabs(den) < 1e-4) den = den >= 0.0 ? 1e-4 : -1e-4;
+        double td = r / den;
+        t[d] = td;
+        rr += r * r;
+        tt += td * td;
+    }
+    rr = warp_sum(rr);
+    tt = warp_sum(tt);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[w] = rr;
+        red[32 + w] = tt;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double s = 0.0;
+        for (int j = 0; j < nw; ++j) s += red[threadIdx.x * 32 + j];
+        partial[(size_t)blockIdx.x * 2 + threadIdx.x] = s;
+    }
+}
+
+// u -= sum_{i<K} coef[i] A_i  (and the same on a second pair when B is not NULL:
+// ub -= sum coef[i] B_i), coefficients read on the device.
+__global__ void k_subtract(const double *A, const double *B, size_t ld, int K, const double *coef, int64_t N,
+                           double *u, double *ub)
+{
+    double cf[LRED];
+#pragma unroll
+    for (int i = 0; i < LRED; ++i) cf[i] = (i < K) ? coef[i] : 0.0;
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < N; d += (int64_t)gridDim.x * blockDim.x) {
+        double s = u[d], sb = ub ? ub[d] : 0.0;
+#pragma unroll
+        for (int i = 0; i < LRED; ++i)
+            if (i < K) {
+                s -= cf[i] * A[i * ld + d];
+                if (ub) sb -= cf[i] * B[i * ld + d];
+            }
+        u[d] = s;
+        if (ub) ub[d] = sb;
+    }
+}
+
+// u = src * scale(norm2), scale = 1/sqrt(norm2[0]); optional second vector.
+__global__ void k_scale_copy(const double *src, const double *src2, const double *norm2, int64_t N, double *u,
+                             double *u2, float *u32)
+{
+    const double s = 1.0 / sqrt(norm2[0]);
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < N; d += (int64_t)gridDim.x * blockDim.x) {
+        double v = src[d] * s;
+        u[d] = v;
+        if (u2) u2[d] = src2[d] * s;
+        if (u32) u32[d] = (float)v;
+    }
+}
+
+__global__ void k_to_float(const double *src, int64_t N, float *dst)
+{
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < N; d += (int64_t)gridDim.x * blockDim.x)
+        dst[d] = (float)src[d];
+}
+
+__global__ void k_copy2(const double *a, const double *b, int64_t N, double *ca, double *cb)
+{
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < N; d += (int64_t)gridDim.x * blockDim.x) {
+        ca[d] = a[d];
+        cb[d] = b[d];
+    }
+}
+
+// start vector: lowest diagonal element (index given) + fixed admixture
+__global__ void k_large_guess(const int64_t *best, int64_t N, double *x)
+{
+    const int64_t bi = best[0];
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < N; d += (int64_t)gridDim.x * blockDim.x)
+        x[d] = (d == bi ? 1.0 : 0.0) + GUESS_NOISE * guess_noise((int)(d & 0x7fffffff));
+}
+
+// index of the smallest diagonal element (ties -> lowest index), one block
+__global__ void k_argmin(const double *diag, int64_t N, int64_t *out)
+{
+    __shared__ double bv[32];
+    __shared__ int64_t bix[32];
+    double best = 1e300;
+    int64_t bi = INT64_MAX;
+    for (int64_t d = threadIdx.x; d < N; d += blockDim.x) {
+        double v = diag[d];
+        if (v < best || (v == best && d < bi)) {
+            best = v;
+            bi = d;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(FULL, best, o);
+        int64_t oi = __shfl_xor_sync(FULL, bi, o);
+        if (ov < best || (ov == best && oi < bi)) {
+            best = ov;
+            bi = oi;
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        bv[w] = best;
+        bix[w] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int j = 1; j < (int)(blockDim.x >> 5); ++j)
+            if (bv[j] < best || (bv[j] == best && bix[j] < bi)) {
+                best = bv[j];
+                bi = bix[j];
+            }
+        out[0] = bi;
+    }
+}
+
+// Projected eigenproblem (one warp) and bookkeeping of G on the device.
+__global__ void k_large_small_eig(const double *Gd, int m, double *ys, double *y2s, double *misc)
+{
+    __shared__ double G[MMAX * MMAX];
+    __shared__ float A[MMAX * MMAX], E[MMAX * MMAX], ev[MMAX];
+    __shared__ double r[MMAX];
+    for (int e = threadIdx.x; e < MMAX * MMAX; e += 32) G[e] = Gd[e];
+    __syncwarp();
+    small_eig_warp<true>(G, m, A, E, ev, ys, y2s, r, misc);
+}
+
+// G column m (and row m) from the dots in `dots` (m + 1 values)
+__global__ void k_set_gcol(double *Gd, int m, const double *dots)
+{
+    int i = threadIdx.x;
+    if (i <= m) {
+        Gd[i * MMAX + m] = dots[i];
+        Gd[m * MMAX + i] = dots[i];
+    }
+}
+
+__global__ void k_set_g2(double *Gd, const double *dots, int two)
+{
+    if (threadIdx.x == 0) {
+        Gd[0] = dots[0];
+        if (two) {
+            Gd[1] = Gd[MMAX] = dots[1];
+            Gd[MMAX + 1] = dots[2];
+        }
+    }
+}
+
+}  // namespace mbe
+
+namespace mbe {
+
+struct LargePlan {
+    LargeCas L;
+    int grid_sigma64, grid_sigma32, grid_vec;
+    size_t smem64, smem32;
+};
+
+// Host-side size of the set-up data; the dense Hs may live in `dense_at` (e.g.
+// the Davidson basis region, unused during set-up).
+static int large_setup(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ, int n_cas,
+                       const int32_t *cas_orbs, Bump &bump, double *dense_at, LargePlan *plan, int *k_out,
+                       int64_t *dphi_out)
+{
+    MBE_CHECK(n_cas >= 1 && n_cas <= MBE_MAX_STRING_ORB && n_cas <= norb, MBE_EUNSUPPORTED,
+              "large CASCI: n_cas %d outside 1..%d", n_cas, MBE_MAX_STRING_ORB);
+    std::vector<int> A(cas_orbs, cas_orbs + n_cas);
+    std::sort(A.begin(), A.end());
+    for (int i = 0; i < n_cas; ++i)
+        MBE_CHECK(A[i] >= 0 && A[i] < norb && (i == 0 || A[i] != A[i - 1]), MBE_EINVAL,
+                  "large CASCI: active orbital %d out of range or repeated", A[i]);
+    std::vector<uint8_t> occ_h(norb);
+    MBE_CU(cudaMemcpyAsync(occ_h.data(), occ, norb, cudaMemcpyDeviceToHost, ctx->stream));
+    MBE_CU(cudaStreamSynchronize(ctx->stream));
+    int k = 0;
+    uint32_t mphi = 0;
+    for (int i = 0; i < n_cas; ++i)
+        if (occ_h[A[i]]) {
+            ++k;
+            mphi |= 1u << i;
+        }
+    const StringTable *st = nullptr;
+    int rc = get_table(ctx, n_cas, k, &st);
+    if (rc) return rc;
+    LargeCas &L = plan->L;
+    L.n = n_cas;
+    L.P = n_cas * (n_cas + 1) / 2;
+    L.k = k;
+    L.Ns = (int)st->ns;
+    L.R = st->r;
+    L.N = st->ns * st->ns;
+    L.str = st->strings;
+    L.tab = st->table;
+    const int P = L.P;
+    const int64_t conn = 1 + (int64_t)k * (n_cas - k) + binom(k, 2) * binom(n_cas - k, 2);
+    double *F = bump.take<double>((size_t)norb * norb);
+    L.V = bump.take<double>((size_t)P * P);
+    L.V32 = bump.take<float>((size_t)P * P);
+    L.hp = bump.take<double>(P);
+    L.pp = bump.take<short>(2 * P);
+    L.roff = bump.take<int64_t>((size_t)L.Ns + 1);
+    L.col = bump.take<int32_t>((size_t)L.Ns * conn);
+    L.val = bump.take<double>((size_t)L.Ns * conn);
+    L.val32 = bump.take<float>((size_t)L.Ns * conn);
+    L.diag = bump.take<double>((size_t)L.N);
+    int32_t *cnt = bump.take<int32_t>((size_t)L.Ns);
+    int64_t *off = bump.take<int64_t>((size_t)L.Ns + 1);
+    L.Hd = dense_at ? dense_at : bump.take<double>((size_t)L.Ns * L.Ns);
+    // (all of the above fits: the caller sized the workspace with large_bytes)
+    k_core_fock<<<(norb * norb + 127) / 128, 128, 0, ctx->stream>>>(norb, h1, eri, occ, F);
+    LargeSetupArgs sa;
+    memset(&sa, 0, sizeof(sa));
+    for (int i = 0; i < n_cas; ++i) sa.A[i] = A[i];
+    sa.norb = norb;
+    sa.eri = eri;
+    sa.occ = occ;
+    sa.F = F;
+    k_large_setup<<<1, CTA_THREADS, 0, ctx->stream>>>(sa, L);
+    k_large_hs_cols<<<(L.Ns + 127) / 128, 128, 0, ctx->stream>>>(L);
+    const unsigned wgrid = (unsigned)(((int64_t)L.Ns * 32 + 255) / 256);
+    k_large_hs_count<<<wgrid, 256, 0, ctx->stream>>>(L, cnt);
+    k_scan_counts<<<1, 256, 0, ctx->stream>>>(cnt, L.Ns, off);
+    k_large_hs_fill<<<wgrid, 256, 0, ctx->stream>>>(L, off);
+    k_large_diag<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(L);
+    MBE_CU(cudaGetLastError());
+    ctx->launches += 7;
+    *k_out = k;
+    int iphi = string_rank(mphi);
+    *dphi_out = (int64_t)iphi * L.Ns + iphi;
+    // launch shapes
+    plan->smem64 = (size_t)P * P * 8;
+    plan->smem32 = (size_t)P * P * 4;
+    MBE_CHECK(plan->smem64 <= ctx->smem_optin, MBE_EUNSUPPORTED, "large CASCI: V needs %zu B shared memory",
+              plan->smem64);
+    MBE_CU(cudaFuncSetAttribute(k_large_sigma<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)plan->smem64));
+    MBE_CU(cudaFuncSetAttribute(k_large_sigma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)plan->smem32));
+    int b64 = 0, b32 = 0;
+    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_large_sigma<double>, SIGMA_THREADS, plan->smem64));
+    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_large_sigma<float>, SIGMA_THREADS, plan->smem32));
+    plan->grid_sigma64 = ctx->sm_count * (b64 > 0 ? b64 : 1);
+    plan->grid_sigma32 = ctx->sm_count * (b32 > 0 ? b32 : 1);
+    plan->grid_vec = ctx->sm_count * 4;
+    return MBE_OK;
+}
+
+// Workspace bytes of large_setup (plus `extra`, and the dense Hs unless aliased).
+static size_t large_bytes(int norb, int n, int k, bool dense_separate)
+{
+    const int64_t ns = binom(n, k), N = ns * ns;
+    const int P = n * (n + 1) / 2;
+    const int64_t conn = 1 + (int64_t)k * (n - k) + binom(k, 2) * binom(n - k, 2);
+    size_t b = align256((size_t)norb * norb * 8) + align256((size_t)P * P * 8) + align256((size_t)P * P * 4) +
+               align256(P * 8) + align256(2 * P * 2) + align256((ns + 1) * 8) + align256(ns * conn * 4) +
+               align256(ns * conn * 8) + align256(ns * conn * 4) + align256(N * 8) + align256(ns * 4) +
+               align256((ns + 1) * 8) + 4096;
+    if (dense_separate) b += align256((size_t)ns * ns * 8);
+    return b;
+}
+
+template <typename T>
+static int large_sigma_launch(mbe_ctx *ctx, const LargePlan &pl, const T *c, double *sigma, int order_tag)
+{
+    TimedLaunch tl(ctx, order_tag, 2, sizeof(T) == 8 ? 64 : 32);
+    if (sizeof(T) == 8)
+        k_large_sigma<double><<<pl.grid_sigma64, SIGMA_THREADS, pl.smem64, ctx->stream>>>(pl.L, (const double *)c,
+                                                                                          sigma);
+    else
+        k_large_sigma<float><<<pl.grid_sigma32, SIGMA_THREADS, pl.smem32, ctx->stream>>>(pl.L, (const float *)c,
+                                                                                         sigma);
+    MBE_CU(cudaGetLastError());
+    ++ctx->launches;
+    return tl.done();
+}
+
+}  // namespace mbe
+
+extern "C" int casci_sigma_large(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
+                                 int n_cas, const int32_t *cas_orbs, int precision, const double *c,
+                                 double *sigma, double *diag)
+{
+    MBE_CHECK(ctx && h1 && eri && occ && cas_orbs && c && sigma, MBE_EINVAL, "casci_sigma_large: NULL argument");
+    MBE_CHECK(norb >= 1 && norb <= MBE_MAX_NORB, MBE_EINVAL, "casci_sigma_large: norb %d", norb);
+    MBE_CHECK(precision == MBE_PREC_FP64 || precision == MBE_PREC_MIXED, MBE_EINVAL,
+              "casci_sigma_large: precision %d", precision);
+    MBE_CU(cudaSetDevice(ctx->device));
+    // occupation count first (sizes depend on it)
+    std::vector<uint8_t> occ_h(norb);
+    MBE_CU(cudaMemcpyAsync(occ_h.data(), occ, norb, cudaMemcpyDeviceToHost, ctx->stream));
+    MBE_CU(cudaStreamSynchronize(ctx->stream));
+    MBE_CHECK(n_cas >= 1 && n_cas <= MBE_MAX_STRING_ORB && n_cas <= norb, MBE_EUNSUPPORTED,
+              "casci_sigma_large: n_cas %d outside 1..%d", n_cas, MBE_MAX_STRING_ORB);
+    int k0 = 0;
+    for (int i = 0; i < n_cas; ++i) k0 += (cas_orbs[i] >= 0 && cas_orbs[i] < norb && occ_h[cas_orbs[i]]) ? 1 : 0;
+    const int64_t N = binom(n_cas, k0) * binom(n_cas, k0);
+    size_t bytes = large_bytes(norb, n_cas, k0, true) + (precision == MBE_PREC_MIXED ? align256(N * 4) : 0);
+    void *ws = nullptr;
+    int rc = workspace(ctx, bytes, &ws);
+    if (rc) return rc;
+    Bump bump(ws);
+    LargePlan pl;
+    int k = 0;
+    int64_t dphi = 0;
+    rc = large_setup(ctx, norb, h1, eri, occ, n_cas, cas_orbs, bump, nullptr, &pl, &k, &dphi);
+    if (rc) return rc;
+    if (diag) MBE_CU(cudaMemcpyAsync(diag, pl.L.diag, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (precision == MBE_PREC_FP64) return large_sigma_launch<double>(ctx, pl, c, sigma, n_cas);
+    float *c32 = bump.take<float>((size_t)N);
+    k_to_float<<<pl.grid_vec, 256, 0, ctx->stream>>>(c, N, c32);
+    ++ctx->launches;
+    return large_sigma_launch<float>(ctx, pl, c32, sigma, n_cas);
+}
+
+namespace mbe {
+
+// x2 = V y2, hx2 = W y2 over the first m basis vectors
+__global__ void k_lincomb2(const double *V, const double *W, size_t ld, int m, const double *ys, int64_t N,
+                           double *x2, double *hx2)
+{
+    double y[MLARGE];
+#pragma unroll
+    for (int i = 0; i < MLARGE; ++i) y[i] = (i < m) ? ys[i] : 0.0;
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < N; d += (int64_t)gridDim.x * blockDim.x) {
+        double xs = 0.0, hs = 0.0;
+#pragma unroll
+        for (int i = 0; i < MLARGE; ++i)
+            if (i < m) {
+                xs += y[i] * V[i * ld + d];
+                hs += y[i] * W[i * ld + d];
+            }
+        x2[d] = xs;
+        hx2[d] = hs;
+    }
+}
+
+struct LargeDav {
+    double *V, *W, *x, *hx, *t, *x2, *hx2, *partial, *dots, *Gd, *ys, *y2s, *misc;
+    float *c32;
+    int64_t *best;
+    size_t ld;
+    int nblk;
+};
+
+static void dot_to(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, const double *A, int K, const double *u,
+                   double *out)
+{
+    k_multidot<<<D.nblk, LARGE_THREADS, 0, ctx->stream>>>(A, D.ld, K, u, pl.L.N, D.partial);
+    k_multidot_final<<<1, 32 * K, 0, ctx->stream>>>(D.partial, D.nblk, K, out);
+    ctx->launches += 2;
+}
+
+template <typename T>
+static int large_apply(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, const double *vin, double *wout)
+{
+    if (sizeof(T) == 8) return large_sigma_launch<double>(ctx, pl, vin, wout, pl.L.n);
+    k_to_float<<<pl.grid_vec, 256, 0, ctx->stream>>>(vin, pl.L.N, D.c32);
+    ++ctx->launches;
+    return large_sigma_launch<float>(ctx, pl, D.c32, wout, pl.L.n);
+}
+
+// One Davidson phase on the large space (T = sigma arithmetic).  D.x: start
+// vector in, Ritz vector out.
+template <typename T>
+static int large_phase(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, double tol, int min_iter,
+                       int max_iter, bool steer, double *lambda, double *rnorm, int *nsig, int *status)
+{
+    const int64_t N = pl.L.N;
+    const size_t ld = D.ld;
+    cudaStream_t st = ctx->stream;
+    const int g = pl.grid_vec;
+    double h3[3];
+    *nsig = 0;
+    *status = MBE_STATUS_OK;
+    int rc;
+    dot_to(ctx, pl, D, D.x, 1, D.x, D.dots);
+    k_scale_copy<<<g, 256, 0, st>>>(D.x, nullptr, D.dots, N, D.V, nullptr, nullptr);
+    ++ctx->launches;
+    if ((rc = large_apply<T>(ctx, pl, D, D.V, D.W))) return rc;
+    ++*nsig;
+    dot_to(ctx, pl, D, D.W, 1, D.V, D.dots);
+    k_set_g2<<<1, 32, 0, st>>>(D.Gd, D.dots, 0);
+    ++ctx->launches;
+    int m = 1;
+    double best = 3e38;
+    int stall = 0;
+    for (int it = 0;; ++it) {
+        k_large_small_eig<<<1, 32, 0, st>>>(D.Gd, m, D.ys, D.y2s, D.misc);
+        double *tdst = (m < MLARGE) ? D.V + (size_t)m * ld : D.t;
+        k_ritz<<<D.nblk, LARGE_THREADS, 0, st>>>(D.V, D.W, ld, m, D.ys, D.misc, pl.L.diag, N, D.x, D.hx, tdst,
+                                                 D.partial);
+        k_multidot_final<<<1, 64, 0, st>>>(D.partial, D.nblk, 2, D.dots);
+        ctx->launches += 3;
+        MBE_CU(cudaMemcpyAsync(h3, D.dots, 16, cudaMemcpyDeviceToHost, st));
+        MBE_CU(cudaMemcpyAsync(h3 + 2, D.misc, 8, cudaMemcpyDeviceToHost, st));
+        MBE_CU(cudaStreamSynchronize(st));
+        const double rn = sqrt(h3[0]), t0n = sqrt(h3[1]);
+        *lambda = h3[2];
+        *rnorm = rn;
+        if (!std::isfinite(rn) || !std::isfinite(h3[2])) {
+            *status = MBE_STATUS_NONFINITE;
+            break;
+        }
+        if (rn <= tol && it >= min_iter) break;
+        if (it >= max_iter) {
+            *status = MBE_STATUS_MAXITER;
+            break;
+        }
+        if (steer) {
+            if (rn < 0.9 * best) {
+                best = rn;
+                stall = 0;
+            } else if (++stall >= 3) {
+                break;
+            }
+        }
+        double *u = D.V + (size_t)m * ld;
+        if (m == MLARGE) {
+            // thick restart on the two lowest Ritz vectors (orthogonal by construction)
+            k_lincomb2<<<g, 256, 0, st>>>(D.V, D.W, ld, m, D.y2s, N, D.x2, D.hx2);
+            k_copy2<<<g, 256, 0, st>>>(D.x, D.hx, N, D.V, D.W);
+            k_copy2<<<g, 256, 0, st>>>(D.x2, D.hx2, N, D.V + ld, D.W + ld);
+            ctx->launches += 3;
+            for (int pass = 0; pass < 2; ++pass) {
+                dot_to(ctx, pl, D, D.V, 1, D.V + ld, D.dots);
+                k_subtract<<<g, 256, 0, st>>>(D.V, D.W, ld, 1, D.dots, N, D.V + ld, D.W + ld);
+                ++ctx->launches;
+            }
+            dot_to(ctx, pl, D, D.V + ld, 1, D.V + ld, D.dots);
+            k_scale_copy<<<g, 256, 0, st>>>(D.V + ld, D.W + ld, D.dots, N, D.V + ld, D.W + ld, nullptr);
+            dot_to(ctx, pl, D, D.W, 2, D.V, D.dots);
+            dot_to(ctx, pl, D, D.W + ld, 1, D.V + ld, D.dots + 2);
+            k_set_g2<<<1, 32, 0, st>>>(D.Gd, D.dots, 1);
+            ctx->launches += 2;
+            m = 2;
+            u = D.V + (size_t)m * ld;
+            MBE_CU(cudaMemcpyAsync(u, D.t, (size_t)N * 8, cudaMemcpyDeviceToDevice, st));
+        }
+        for (int pass = 0; pass < 2; ++pass) {
+            dot_to(ctx, pl, D, D.V, m, u, D.dots);
+            k_subtract<<<g, 256, 0, st>>>(D.V, nullptr, ld, m, D.dots, N, u, nullptr);
+            ++ctx->launches;
+        }
+        dot_to(ctx, pl, D, u, 1, u, D.dots);
+        MBE_CU(cudaMemcpyAsync(h3, D.dots, 8, cudaMemcpyDeviceToHost, st));
+        MBE_CU(cudaStreamSynchronize(st));
+        const double tn = sqrt(h3[0]);
+        if (!(tn > 1e-12 * t0n) || !(tn > 0.0)) {
+            if (!steer && rn > tol) *status = MBE_STATUS_MAXITER;
+            break;
+        }
+        k_scale_copy<<<g, 256, 0, st>>>(u, nullptr, D.dots, N, u, nullptr, nullptr);
+        ++ctx->launches;
+        if ((rc = large_apply<T>(ctx, pl, D, u, D.W + (size_t)m * ld))) return rc;
+        ++*nsig;
+        dot_to(ctx, pl, D, D.V, m + 1, D.W + (size_t)m * ld, D.dots);
+        k_set_gcol<<<1, 32, 0, st>>>(D.Gd, m, D.dots);
+        ++ctx->launches;
+        ++m;
+    }
+    return MBE_OK;
+}
+
+}  // namespace mbe
+
+extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
+                           int n_cas, const int32_t *cas_orbs, const mbe_opts *opts, double *result,
+                           int32_t *info, double *cvec)
+{
+    MBE_CHECK(ctx && h1 && eri && occ && cas_orbs && result && info, MBE_EINVAL, "casci_solve: NULL argument");
+    MBE_CHECK(norb >= 1 && norb <= MBE_MAX_NORB, MBE_EINVAL, "casci_solve: norb %d", norb);
+    MBE_CHECK(n_cas >= 1 && n_cas <= MBE_MAX_STRING_ORB && n_cas <= norb, MBE_EUNSUPPORTED,
+              "casci_solve: n_cas %d outside 1..%d", n_cas, MBE_MAX_STRING_ORB);
+    mbe_opts o;
+    if (opts) o = *opts; else mbe_default_opts(&o);
+    MBE_CHECK(o.precision == MBE_PREC_FP64 || o.precision == MBE_PREC_MIXED, MBE_EINVAL,
+              "casci_solve: unknown precision %d", o.precision);
+    MBE_CHECK(o.tol > 0 && o.tol_switch > 0 && o.max_iter >= 1 && o.fp64_final_iters >= 0, MBE_EINVAL,
+              "casci_solve: bad options");
+    MBE_CU(cudaSetDevice(ctx->device));
+    std::vector<uint8_t> occ_h(norb);
+    MBE_CU(cudaMemcpyAsync(occ_h.data(), occ, norb, cudaMemcpyDeviceToHost, ctx->stream));
+    MBE_CU(cudaStreamSynchronize(ctx->stream));
+    int k0 = 0;
+    for (int i = 0; i < n_cas; ++i) k0 += (cas_orbs[i] >= 0 && cas_orbs[i] < norb && occ_h[cas_orbs[i]]) ? 1 : 0;
+    const int64_t N = binom(n_cas, k0) * binom(n_cas, k0);
+    const size_t vec = align256((size_t)N * 8);
+    LargeDav D;
+    D.ld = vec / 8;
+    D.nblk = ctx->sm_count * 4;
+    size_t bytes = large_bytes(norb, n_cas, k0, false) + vec * (2 * MLARGE + 5) + align256((size_t)N * 4) +
+                   align256((size_t)D.nblk * LRED * 8) + 8 * 256 + 4096;
+    void *ws = nullptr;
+    int rc = workspace(ctx, bytes, &ws);
+    if (rc) return rc;
+    Bump bump(ws);
+    D.V = bump.take<double>(D.ld * MLARGE);
+    D.W = bump.take<double>(D.ld * MLARGE);
+    D.x = bump.take<double>(D.ld);
+    D.hx = bump.take<double>(D.ld);
+    D.t = bump.take<double>(D.ld);
+    D.x2 = bump.take<double>(D.ld);
+    D.hx2 = bump.take<double>(D.ld);
+    D.c32 = bump.take<float>((size_t)N);
+    D.partial = bump.take<double>((size_t)D.nblk * LRED);
+    D.dots = bump.take<double>(32);
+    D.Gd = bump.take<double>(MMAX * MMAX);
+    D.ys = bump.take<double>(MMAX);
+    D.y2s = bump.take<double>(MMAX);
+    D.misc = bump.take<double>(8);
+    D.best = bump.take<int64_t>(4);
+    LargePlan pl;
+    int k = 0;
+    int64_t dphi = 0;
+    // The dense one-spin Hamiltonian of the set-up lives in the (not yet used) basis region.
+    rc = large_setup(ctx, norb, h1, eri, occ, n_cas, cas_orbs, bump, D.V, &pl, &k, &dphi);
+    if (rc) return rc;
+    k_argmin<<<1, 1024, 0, ctx->stream>>>(pl.L.diag, N, D.best);
+    k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best, N, D.x);
+    ctx->launches += 2;
+    double lam = 0.0, rn = 0.0;
+    int n32 = 0, n64 = 0, st32 = 0, st = 0;
+    const bool mixed = o.precision == MBE_PREC_MIXED;
+    if (mixed) {
+        rc = large_phase<float>(ctx, pl, D, o.tol_switch, 0, o.max_iter, true, &lam, &rn, &n32, &st32);
+        if (rc) return rc;
+        if (st32 == MBE_STATUS_NONFINITE) {
+            k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best, N, D.x);
+            ++ctx->launches;
+        }
+    }
+    rc = large_phase<double>(ctx, pl, D, o.tol, mixed ? o.fp64_final_iters : 0, o.max_iter, false, &lam, &rn, &n64,
+                             &st);
+    if (rc) return rc;
+    double ephi = 0.0;
+    MBE_CU(cudaMemcpyAsync(&ephi, pl.L.diag + dphi, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (cvec) MBE_CU(cudaMemcpyAsync(cvec, D.x, (size_t)N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    MBE_CU(cudaStreamSynchronize(ctx->stream));
+    result[0] = lam;
+    result[1] = lam - ephi;
+    result[2] = rn;
+    info[0] = st;
+    info[1] = n64;
+    info[2] = n32;
+    return MBE_OK;
 }
