@@ -121,6 +121,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(values, device=None):
+    """Element-wise maximum of a list of floats over all ranks (identity for one
+    rank).  The timed region of every rank is compared, so the slowest rank sets
+    the whole-job time."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(values)
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.cpu().tolist()
+
+
+def whole_job_rate(units_per_rank: int, world_size: int, ms_per_step_max: float) -> float:
+    """Units all ranks processed per second: every rank runs its own replica."""
+    return world_size * units_per_rank / (ms_per_step_max / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -267,17 +286,12 @@ def run_ours(args):
     ms_64, out_64, recs_64, _ = timed(fp64)
     clocks = sampler.stop()
 
-    tot_mix = torch.tensor([sum(ms_mix)], dtype=torch.float64, device=dev)
-    tot_64 = torch.tensor([sum(ms_64)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(tot_mix, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tot_64, op=dist.ReduceOp.MAX)
+    tot_mix, tot_64 = max_over_ranks([sum(ms_mix), sum(ms_64)], device=dev)
     n_tuples = sum(int(t.shape[0]) for t in out_mix["tuples"])
-    ms_step_mix = tot_mix.item() / args.steps
-    ms_step_64 = tot_64.item() / args.steps
-    value_mix = ws * n_tuples / (ms_step_mix / 1e3)
-    value_64 = ws * n_tuples / (ms_step_64 / 1e3)
+    ms_step_mix = tot_mix / args.steps
+    ms_step_64 = tot_64 / args.steps
+    value_mix = whole_job_rate(n_tuples, ws, ms_step_mix)
+    value_64 = whole_job_rate(n_tuples, ws, ms_step_64)
 
     # accuracy of the mixed form against float64 on the same tuples
     diff = max([float((a - b).abs().max().item()) for a, b in zip(out_mix["eps"], out_64["eps"])
@@ -485,14 +499,15 @@ def run_large(args):
         del c
         torch.cuda.empty_cache()
     solves = {}
-    for prec in ("mixed", "fp64"):
+    for prec in (() if args.no_solve else ("mixed", "fp64")):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         res = ctx.casci_solve(th1, teri, tocc, actives[12], eng.Opts(precision=prec, tol=1e-8))
         torch.cuda.synchronize()
         solves[prec] = dict(res, seconds=time.perf_counter() - t0)
     out["solve_12o"] = solves
-    out["solve_12o"]["abs_diff_lambda"] = abs(solves["mixed"]["lam"] - solves["fp64"]["lam"])
+    if solves:
+        out["solve_12o"]["abs_diff_lambda"] = abs(solves["mixed"]["lam"] - solves["fp64"]["lam"])
     print(json.dumps(out))
     ctx.close()
 
@@ -513,6 +528,7 @@ def main():
     ap.add_argument("--large", action="store_true",
                     help="single large CASCI: sigma throughput at 12/14/16 orbitals and a 12-orbital solve")
     ap.add_argument("--large-sizes", type=int, nargs="+", default=[12, 14, 16])
+    ap.add_argument("--no-solve", action="store_true", help="--large: skip the 12-orbital Davidson solves")
     args = ap.parse_args()
     if args.large:
         run_large(args)
