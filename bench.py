@@ -502,7 +502,7 @@ def run_large(args):
     for prec in (() if args.no_solve else ("mixed", "fp64")):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = ctx.casci_solve(th1, teri, tocc, actives[12], eng.Opts(precision=prec, tol=1e-8))
+        res = ctx.casci_solve(th1, teri, tocc, actives[12], eng.Opts(precision=prec, tol=1e-8, max_iter=3000))
         torch.cuda.synchronize()
         solves[prec] = dict(res, seconds=time.perf_counter() - t0)
     out["solve_12o"] = solves
