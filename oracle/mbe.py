@@ -30,6 +30,25 @@ Tuples of order n are all n-subsets of the sorted expansion space in
 lexicographic order.  With the skip rule (the vacuum-reference statement after
 Eq. 3: only tuples holding both occupied and virtual orbitals contribute), a
 tuple is dropped when A = R u Omega holds no occupied or no virtual orbital.
+
+Screened expansion (Sec. 2, the child-spawning rule and Eq. 4):
+
+* Eq. 4: a tuple's threshold is T_tup = 0 when M_tup < M_init and
+  T_init * a^(M_tup - M_init) otherwise, with M_tup = max(number of occupied,
+  number of virtual orbitals of the tuple Omega);
+* the first order of the expansion (order 2 for an empty reference space with
+  the skip rule, order 1 otherwise) holds every tuple; an order-(k+1) tuple is
+  spawned when the absolute increment of at least one of its order-k sub-tuples
+  exceeds the child's threshold, a sub-tuple that was not computed (skipped or
+  not spawned) counting as zero; the skip rule still applies to the child.
+  (The paper phrases this per parent tuple and candidate orbital; read as a
+  condition on the child's order-k sub-tuples it does not depend on which
+  parent generates the child.)
+
+Pins (tests/test_oracle_pins.py): zero thresholds reproduce the complete tuple
+sets and the unscreened energies, an unreachable threshold stops the expansion
+after its first order, a hand-worked four-orbital example, Eq. 4 at hand-computed
+points, monotonicity in a, and brute-force versus parent-driven enumeration.
 """
 
 from __future__ import annotations
@@ -170,3 +189,63 @@ def run_mbe(h1, eri, occ, ref, exp, orders, skip: bool):
     e_corr = math.fsum([e_ref] + [e_order[n] for n in orders])
     return dict(e_phi=e_phi, e_ref_corr=e_ref, eps=eps_by_order, inc=inc, e_order=e_order,
                 e_corr=e_corr, e_tot=e_phi + e_corr)
+
+
+def tuple_threshold(tup: Sequence[int], occ: np.ndarray, t_init: float, m_init: int, a: float) -> float:
+    """Eq. 4: T_tup = 0 if M_tup < M_init, else T_init * a^(M_tup - M_init)."""
+    n_occ = sum(1 for p in tup if occ[p])
+    m_tup = max(n_occ, len(tup) - n_occ)
+    if m_tup < m_init:
+        return 0.0
+    t = float(t_init)
+    for _ in range(m_tup - m_init):  # repeated products, in this order
+        t *= a
+    return t
+
+
+def first_order(ref: Sequence[int], skip: bool) -> int:
+    """Lowest order with computed tuples: 2 for an empty reference space under the
+    skip rule (no single orbital is both occupied and virtual), else 1."""
+    return 2 if (skip and len(ref) == 0) else 1
+
+
+def spawn(exp: Sequence[int], ref: Sequence[int], occ: np.ndarray, order: int,
+          inc: Dict[Tuple[int, ...], float], skip: bool, t_init: float, m_init: int,
+          a: float) -> List[Tuple[int, ...]]:
+    """Order-(order+1) tuples spawned from the order-`order` increments `inc`
+    (all (order+1)-subsets tested, lexicographic output)."""
+    out = []
+    for child in itertools.combinations(sorted(exp), order + 1):
+        if skip and not keep_tuple(child, ref, occ):
+            continue
+        best = max(abs(inc.get(s, 0.0)) for s in itertools.combinations(child, order))
+        if best > tuple_threshold(child, occ, t_init, m_init, a):
+            out.append(child)
+    return out
+
+
+def run_mbe_screened(h1, eri, occ, ref, exp, max_order: int, skip: bool, t_init: float = 1e-10,
+                     m_init: int = 3, a: float = 5.0):
+    """Screened MBE: complete first order, then spawned orders until max_order or
+    until no tuple is spawned."""
+    e_phi = phi_energy(h1, eri, occ)
+    e_ref = ref_corr_energy(h1, eri, occ, ref)
+    k0 = first_order(ref, skip)
+    eps_by_order: Dict[int, Dict[Tuple[int, ...], float]] = {}
+    inc: Dict[Tuple[int, ...], float] = {}
+    tups = tuples(exp, ref, occ, k0, skip)
+    orders = []
+    for k in range(k0, max_order + 1):
+        if k > k0:
+            tups = spawn(exp, ref, occ, k - 1, {t: inc[t] for t in eps_by_order[k - 1]}, skip,
+                         t_init, m_init, a)
+        if not tups:
+            break
+        eps_by_order[k] = {t: tuple_energy(h1, eri, occ, ref, t, e_phi, e_ref) for t in tups}
+        inc = increments(eps_by_order)
+        orders.append(k)
+    e_order = order_sums(inc, orders)
+    e_corr = math.fsum([e_ref] + [e_order[n] for n in orders])
+    return dict(e_phi=e_phi, e_ref_corr=e_ref, eps=eps_by_order, inc=inc, e_order=e_order,
+                e_corr=e_corr, e_tot=e_phi + e_corr, orders=orders,
+                tuples={n: list(eps_by_order[n]) for n in orders})
