@@ -2040,10 +2040,14 @@ extern "C" int casci_sigma_noalloc(int device, void *cuda_stream, int norb, cons
 //   * set-up: h_eff, packed V, h' (one block); the one-spin Hamiltonian Hs built
 //     column-parallel over the grid as a dense Ns x Ns matrix, then compressed to
 //     CSR (each row holds the strings connected by at most a double replacement);
-//   * sigma: one thread per determinant; Hs C and C Hs^T through the CSR rows
-//     (the first one coalesced over the beta index), the opposite-spin term as the
-//     direct double loop over replacement lists with V staged in shared memory;
-//     float32 or float64 arithmetic;
+//   * sigma = (Hs x 1) c + (1 x Hs) c + opposite-spin term.  The same-spin terms
+//     are row-streamed sparse products C' = Hs C (coalesced over the second
+//     index), the beta one applied to the transposed coefficient matrix and added
+//     back transposed.  The opposite-spin term is, in float64, the direct double
+//     loop over the alpha and beta replacement lists (one thread per determinant,
+//     V in shared memory); in float32 it is, per alpha string, a dense product of
+//     the signed V columns with the gathered rows of C followed by a scatter
+//     through the beta lists into a shared-memory sigma row;
 //   * Davidson: the tuple solvers' algorithm (MLARGE-vector basis, thick restart
 //     on the two lowest Ritz vectors, float32 phase then float64 phase) with its
 //     vector algebra in grid-wide kernels, the projected eigenproblem in one
@@ -2073,9 +2077,9 @@ struct LargeCas {
     float *val32;   // CSR [nnz]
     double *diag;   // [N]
     int64_t nnz;
+    const int32_t *tabT;  // beta lists transposed: tabT[y * Ns + J] = tab[J * R + y]
 };
 
-__global__ void k_scan_counts(const int32_t *counts, int64_t nblocks, int64_t *offsets);
 
 struct LargeSetupArgs {
     int norb;
@@ -2206,48 +2210,218 @@ __global__ void k_large_diag(LargeCas L)
     }
 }
 
-// sigma = H c over the whole determinant space; T is the arithmetic type, c is
-// read as T (a float copy in the float32 phase), sigma is written as float64.
-template <typename T>
-__global__ void __launch_bounds__(SIGMA_THREADS) k_large_sigma(LargeCas L, const T *__restrict__ c,
-                                                                double *__restrict__ sigma)
+// Opposite-spin part of sigma in float64, one thread per determinant:
+//     sigma[Ia][Ib] = sum_{x in list(Ia)} s_x sum_{y in list(Ib)} s_y V[p_x][p_y] c[J_x][J_y]
+// (written, not accumulated). The beta lists are read through the transposed
+// table, so a warp's 32 consecutive Ib load 32 consecutive words.
+__global__ void __launch_bounds__(SIGMA_THREADS) k_large_ab64(LargeCas L, const double *__restrict__ c,
+                                                               double *__restrict__ sigma)
 {
     extern __shared__ __align__(16) char smem[];
-    T *Vs = (T *)smem;
+    double *Vs = (double *)smem;
     const int P = L.P, Ns = L.Ns, R = L.R;
-    const T *Vg = sizeof(T) == 8 ? (const T *)L.V : (const T *)L.V32;
-    const T *val = sizeof(T) == 8 ? (const T *)L.val : (const T *)L.val32;
-    for (int e = threadIdx.x; e < P * P; e += blockDim.x) Vs[e] = Vg[e];
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) Vs[e] = L.V[e];
     __syncthreads();
     for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < L.N; d += (int64_t)gridDim.x * blockDim.x) {
         const int ia = (int)(d / Ns), ib = (int)(d - (int64_t)ia * Ns);
-        T acc0 = 0, acc1 = 0;
-        for (int64_t e = L.roff[ia]; e < L.roff[ia + 1]; ++e)
-            acc0 = fma(val[e], c[(int64_t)L.col[e] * Ns + ib], acc0);
-        const T *crow = c + (int64_t)ia * Ns;
-        for (int64_t e = L.roff[ib]; e < L.roff[ib + 1]; ++e) acc1 = fma(val[e], crow[L.col[e]], acc1);
+        double acc0 = 0.0, acc1 = 0.0;
         const int32_t *ta = L.tab + (size_t)ia * R;
-        const int32_t *tb = L.tab + (size_t)ib * R;
+        const int32_t *tb = L.tabT + ib;
         for (int x = 0; x < R; ++x) {
             const int ea = ta[x];
-            const T *vrow = Vs + entry_pair(ea) * P;
-            const T *cr = c + (int64_t)entry_J(ea) * Ns;
-            T s0 = 0, s1 = 0;
+            const double *vrow = Vs + entry_pair(ea) * P;
+            const double *cr = c + (int64_t)entry_J(ea) * Ns;
+            double s0 = 0.0, s1 = 0.0;
             int y = 0;
             for (; y + 1 < R; y += 2) {
-                const int e0 = tb[y], e1 = tb[y + 1];
+                const int e0 = tb[(size_t)y * Ns], e1 = tb[(size_t)(y + 1) * Ns];
                 s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), cr[entry_J(e0)], s0);
                 s1 = fma(flip_if(vrow[entry_pair(e1)], entry_neg(e1)), cr[entry_J(e1)], s1);
             }
             if (y < R) {
-                const int e0 = tb[y];
+                const int e0 = tb[(size_t)y * Ns];
                 s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), cr[entry_J(e0)], s0);
             }
-            const T s = s0 + s1;
+            const double s = s0 + s1;
             if (x & 1) acc1 += flip_if(s, entry_neg(ea)); else acc0 += flip_if(s, entry_neg(ea));
         }
-        sigma[d] = (double)(acc0 + acc1);
+        sigma[d] = acc0 + acc1;
     }
+}
+
+// Opposite-spin part of sigma in float32, one CTA per alpha string Ia at a time
+// (written, not accumulated):
+//     T[p][Jb] = sum_{x in list(Ia)} A[x][p] c[J_x][Jb],    A[x][p] = s_x V[p_x][p],
+//     sigma[Ia][K] += s T[p][Jb]  for every (Jb, p) with inv[p][Jb] = (K, s),
+// where inv reads the beta lists backwards (E_pq|Jb> = s|K> iff E_qp|K> = s|Jb>;
+// each packed pair occurs at most once in a string's list). Warp w owns the
+// eight rows p = 8w..8w+7 of a T tile, lane l its columns 4l..4l+3; the tile of
+// c rows is prefetched into registers while the previous tile is multiplied.
+constexpr int AB_TJ = 128;  // columns of a T tile
+constexpr int AB_PF = 20;   // prefetched tile words per thread (host-checked)
+constexpr int AB_MAX_THREADS = 576;  // 4 x the padded pair count at 16 orbitals, rounded up
+
+__global__ void __launch_bounds__(AB_MAX_THREADS) k_large_ab32(LargeCas L, int Pp, int Nsp, const float *__restrict__ c,
+                                                    const int32_t *__restrict__ inv, double *__restrict__ sigma)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int P = L.P, Ns = L.Ns, R = L.R;
+    const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    float *A = (float *)smem;                 // [R][Pp]
+    float *B = A + (size_t)R * Pp;            // [R][AB_TJ]
+    float *srow = B + (size_t)R * AB_TJ;      // [Ns]
+    int *Jx = (int *)(srow + Ns);             // [R]
+    const int p0 = 8 * w, j0 = 4 * lane;
+    const int nB = R * AB_TJ;
+    for (int Ia = blockIdx.x; Ia < Ns; Ia += gridDim.x) {
+        const int32_t *ta = L.tab + (size_t)Ia * R;
+        for (int i = tid; i < Ns; i += nt) srow[i] = 0.f;
+        for (int x = tid; x < R; x += nt) Jx[x] = entry_J(ta[x]);
+        for (int i = tid; i < R * Pp; i += nt) {
+            const int x = i / Pp, p = i - x * Pp;
+            const int e = ta[x];
+            A[i] = p < P ? flip_if(L.V32[entry_pair(e) * P + p], entry_neg(e)) : 0.f;
+        }
+        __syncthreads();
+        float pf[AB_PF];
+#pragma unroll
+        for (int k = 0; k < AB_PF; ++k) {
+            const int i = tid + k * nt;
+            const int x = i / AB_TJ, j = i - x * AB_TJ;
+            pf[k] = (i < nB && j < Ns) ? c[(size_t)Jx[x] * Ns + j] : 0.f;
+        }
+        for (int Jb0 = 0; Jb0 < Ns; Jb0 += AB_TJ) {
+#pragma unroll
+            for (int k = 0; k < AB_PF; ++k) {
+                const int i = tid + k * nt;
+                if (i < nB) B[i] = pf[k];
+            }
+            __syncthreads();
+            const int nxt = Jb0 + AB_TJ;
+            if (nxt < Ns) {
+#pragma unroll
+                for (int k = 0; k < AB_PF; ++k) {
+                    const int i = tid + k * nt;
+                    const int x = i / AB_TJ, j = nxt + (i - x * AB_TJ);
+                    pf[k] = (i < nB && j < Ns) ? c[(size_t)Jx[x] * Ns + j] : 0.f;
+                }
+            }
+            float acc[8][4];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+            for (int x = 0; x < R; ++x) {
+                const float4 a0 = *(const float4 *)(A + (size_t)x * Pp + p0);
+                const float4 a1 = *(const float4 *)(A + (size_t)x * Pp + p0 + 4);
+                const float4 b = *(const float4 *)(B + (size_t)x * AB_TJ + j0);
+                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int p = p0 + i;
+                if (p < P) {
+                    const int4 e4 = *(const int4 *)(inv + (size_t)p * Nsp + Jb0 + j0);
+                    const int ev[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (ev[j] >= 0) atomicAdd(&srow[ev[j] >> 1], flip_if(acc[i][j], ev[j] & 1));
+                }
+            }
+            __syncthreads();
+        }
+        for (int K = tid; K < Ns; K += nt) sigma[(size_t)Ia * Ns + K] = (double)srow[K];
+        __syncthreads();
+    }
+}
+
+// Same-spin part, row-streamed: out[I][K] += sum_e val[e] X[col[e]][K] over the
+// CSR row I of Hs, for a block of SS_ROWS rows and a tile of SS_TK columns per
+// work item. Column tiles are the outer work index, so the CTAs in flight share
+// one slab of X in L2. With TRANS the result is added at out[K][I] (X is the
+// transposed coefficient matrix and the product is C Hs^T).
+constexpr int SS_ROWS = 32, SS_TK = 256, SS_THREADS = 256;
+
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(SS_THREADS) k_large_ss(LargeCas L, const T *__restrict__ X,
+                                                          double *__restrict__ sigma)
+{
+    extern __shared__ __align__(16) char smem[];
+    T *out = (T *)smem;  // [SS_ROWS][SS_TK + 1]
+    const int Ns = L.Ns, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const T *val = sizeof(T) == 8 ? (const T *)L.val : (const T *)L.val32;
+    const int nrb = (Ns + SS_ROWS - 1) / SS_ROWS, nct = (Ns + SS_TK - 1) / SS_TK;
+    for (int item = blockIdx.x; item < nrb * nct; item += gridDim.x) {
+        const int ct = item / nrb, rb = item - ct * nrb;
+        const int I0 = rb * SS_ROWS, K0 = ct * SS_TK;
+        for (int r = w; r < SS_ROWS; r += SS_THREADS / 32) {
+            const int I = I0 + r;
+            T acc[SS_TK / 32];
+#pragma unroll
+            for (int j = 0; j < SS_TK / 32; ++j) acc[j] = 0;
+            if (I < Ns) {
+                const int64_t e1 = L.roff[I + 1];
+                for (int64_t e = L.roff[I]; e < e1; ++e) {
+                    const T v = val[e];
+                    const T *xr = X + (size_t)L.col[e] * Ns + K0 + lane;
+#pragma unroll
+                    for (int j = 0; j < SS_TK / 32; ++j)
+                        if (K0 + lane + 32 * j < Ns) acc[j] = fma(v, xr[32 * j], acc[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < SS_TK / 32; ++j) out[r * (SS_TK + 1) + lane + 32 * j] = acc[j];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < SS_ROWS * SS_TK; i += SS_THREADS) {
+            const int r = TRANS ? (i & (SS_ROWS - 1)) : i / SS_TK;
+            const int k = TRANS ? i / SS_ROWS : (i & (SS_TK - 1));
+            const int I = I0 + r, K = K0 + k;
+            if (I < Ns && K < Ns) {
+                const size_t at = TRANS ? (size_t)K * Ns + I : (size_t)I * Ns + K;
+                sigma[at] += (double)out[r * (SS_TK + 1) + k];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// out = in^T for an Ns x Ns matrix, 32 x 32 tiles through shared memory.
+template <typename T>
+__global__ void k_large_transpose(const T *__restrict__ in, int Ns, T *__restrict__ out)
+{
+    __shared__ T tile[32][33];
+    const int nt = (Ns + 31) / 32;
+    for (int64_t t = blockIdx.x; t < (int64_t)nt * nt; t += gridDim.x) {
+        const int bi = (int)(t / nt), bj = (int)(t - (int64_t)bi * nt);
+        for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+            const int i = bi * 32 + r, j = bj * 32 + threadIdx.x;
+            if (i < Ns && j < Ns) tile[r][threadIdx.x] = in[(size_t)i * Ns + j];
+        }
+        __syncthreads();
+        for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+            const int j = bj * 32 + r, i = bi * 32 + threadIdx.x;
+            if (i < Ns && j < Ns) out[(size_t)j * Ns + i] = tile[threadIdx.x][r];
+        }
+        __syncthreads();
+    }
+}
+
+// tabT[y * Ns + J] = tab[J * R + y]; inv[p * Nsp + J] = (K << 1) | neg for the
+// entry (K, p, neg) of J's list (inv preset to -1).
+__global__ void k_large_tables(LargeCas L, int32_t *tabT, int Nsp, int32_t *inv)
+{
+    for (int J = blockIdx.x * blockDim.x + threadIdx.x; J < L.Ns; J += gridDim.x * blockDim.x)
+        for (int y = 0; y < L.R; ++y) {
+            const int e = L.tab[(size_t)J * L.R + y];
+            tabT[(size_t)y * L.Ns + J] = e;
+            if (inv) inv[(size_t)entry_pair(e) * Nsp + J] = (entry_J(e) << 1) | entry_neg(e);
+        }
 }
 
 // ---- grid-wide vector algebra of the large Davidson (all float64)
@@ -2472,14 +2646,19 @@ namespace mbe {
 
 struct LargePlan {
     LargeCas L;
-    int grid_sigma64, grid_sigma32, grid_vec;
-    size_t smem64, smem32;
+    int grid_ab64, grid_ab32, grid_ss64, grid_ss32, grid_vec, grid_tr;
+    size_t smem_ab64, smem_ab32, smem_ss64, smem_ss32;
+    int Pp, Nsp, ab32_threads;
+    int32_t *inv;  // float32 form only: beta lists read backwards [P][Nsp]
+    void *cT;      // transposed coefficients (room for N float64)
 };
 
-// Host-side size of the set-up data; the dense Hs may live in `dense_at` (e.g.
-// the Davidson basis region, unused during set-up).
+static int64_t large_nsp(int64_t ns) { return (ns + AB_TJ - 1) / AB_TJ * AB_TJ; }
+
+// Sets up one large CAS; the dense Hs may live in `dense_at` (e.g. the Davidson
+// basis region, unused during set-up). `fp32` adds the float32 sigma's tables.
 static int large_setup(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ, int n_cas,
-                       const int32_t *cas_orbs, Bump &bump, double *dense_at, LargePlan *plan, int *k_out,
+                       const int32_t *cas_orbs, Bump &bump, double *dense_at, bool fp32, LargePlan *plan, int *k_out,
                        int64_t *dphi_out)
 {
     MBE_CHECK(n_cas >= 1 && n_cas <= MBE_MAX_STRING_ORB && n_cas <= norb, MBE_EUNSUPPORTED,
@@ -2525,6 +2704,12 @@ static int large_setup(mbe_ctx *ctx, int norb, const double *h1, const double *e
     L.diag = bump.take<double>((size_t)L.N);
     int32_t *cnt = bump.take<int32_t>((size_t)L.Ns);
     int64_t *off = bump.take<int64_t>((size_t)L.Ns + 1);
+    int32_t *tabT = bump.take<int32_t>((size_t)L.R * L.Ns);
+    L.tabT = tabT;
+    plan->Pp = (P + 7) / 8 * 8;
+    plan->Nsp = (int)large_nsp(L.Ns);
+    plan->inv = fp32 ? bump.take<int32_t>((size_t)P * plan->Nsp) : nullptr;
+    plan->cT = bump.take<double>((size_t)L.N);  // float32 or float64 use
     L.Hd = dense_at ? dense_at : bump.take<double>((size_t)L.Ns * L.Ns);
     // (all of the above fits: the caller sized the workspace with large_bytes)
     k_core_fock<<<(norb * norb + 127) / 128, 128, 0, ctx->stream>>>(norb, h1, eri, occ, F);
@@ -2542,31 +2727,53 @@ static int large_setup(mbe_ctx *ctx, int norb, const double *h1, const double *e
     k_scan_counts<<<1, 256, 0, ctx->stream>>>(cnt, L.Ns, off);
     k_large_hs_fill<<<wgrid, 256, 0, ctx->stream>>>(L, off);
     k_large_diag<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(L);
+    if (plan->inv)
+        MBE_CU(cudaMemsetAsync(plan->inv, 0xff, (size_t)P * plan->Nsp * sizeof(int32_t), ctx->stream));
+    k_large_tables<<<(L.Ns + 255) / 256, 256, 0, ctx->stream>>>(L, tabT, plan->Nsp, plan->inv);
     MBE_CU(cudaGetLastError());
-    ctx->launches += 7;
+    ctx->launches += 8;
     *k_out = k;
     int iphi = string_rank(mphi);
     *dphi_out = (int64_t)iphi * L.Ns + iphi;
     // launch shapes
-    plan->smem64 = (size_t)P * P * 8;
-    plan->smem32 = (size_t)P * P * 4;
-    MBE_CHECK(plan->smem64 <= ctx->smem_optin, MBE_EUNSUPPORTED, "large CASCI: V needs %zu B shared memory",
-              plan->smem64);
-    MBE_CU(cudaFuncSetAttribute(k_large_sigma<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)plan->smem64));
-    MBE_CU(cudaFuncSetAttribute(k_large_sigma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)plan->smem32));
-    int b64 = 0, b32 = 0;
-    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_large_sigma<double>, SIGMA_THREADS, plan->smem64));
-    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_large_sigma<float>, SIGMA_THREADS, plan->smem32));
-    plan->grid_sigma64 = ctx->sm_count * (b64 > 0 ? b64 : 1);
-    plan->grid_sigma32 = ctx->sm_count * (b32 > 0 ? b32 : 1);
+    plan->smem_ab64 = (size_t)P * P * 8;
+    MBE_CHECK(plan->smem_ab64 <= ctx->smem_optin, MBE_EUNSUPPORTED, "large CASCI: V needs %zu B shared memory",
+              plan->smem_ab64);
+    MBE_CU(cudaFuncSetAttribute(k_large_ab64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem_ab64));
+    int b = 0;
+    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_large_ab64, SIGMA_THREADS, plan->smem_ab64));
+    plan->grid_ab64 = ctx->sm_count * (b > 0 ? b : 1);
+    plan->smem_ss64 = (size_t)SS_ROWS * (SS_TK + 1) * 8;
+    plan->smem_ss32 = (size_t)SS_ROWS * (SS_TK + 1) * 4;
+    MBE_CU(cudaFuncSetAttribute(k_large_ss<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)plan->smem_ss64));
+    MBE_CU(cudaFuncSetAttribute(k_large_ss<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)plan->smem_ss64));
+    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_large_ss<double, false>, SS_THREADS, plan->smem_ss64));
+    plan->grid_ss64 = ctx->sm_count * (b > 0 ? b : 1);
+    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_large_ss<float, false>, SS_THREADS, plan->smem_ss32));
+    plan->grid_ss32 = ctx->sm_count * (b > 0 ? b : 1);
+    plan->grid_tr = ctx->sm_count * 8;
+    if (fp32) {
+        const int R = L.R, Pp = plan->Pp;
+        plan->ab32_threads = 4 * Pp;  // one warp per 8 rows of a T tile
+        MBE_CHECK(plan->ab32_threads <= AB_MAX_THREADS, MBE_EUNSUPPORTED, "large CASCI: %d pairs", P);
+        MBE_CHECK((int64_t)R * AB_TJ <= (int64_t)AB_PF * plan->ab32_threads, MBE_EUNSUPPORTED,
+                  "large CASCI: %d list entries exceed the float32 sigma's prefetch", R);
+        plan->smem_ab32 = (size_t)R * Pp * 4 + (size_t)R * AB_TJ * 4 + (size_t)L.Ns * 4 + (size_t)R * 4;
+        MBE_CHECK(plan->smem_ab32 <= ctx->smem_optin, MBE_EUNSUPPORTED,
+                  "large CASCI: float32 sigma needs %zu B shared memory", plan->smem_ab32);
+        MBE_CU(cudaFuncSetAttribute(k_large_ab32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)plan->smem_ab32));
+        MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_large_ab32, plan->ab32_threads, plan->smem_ab32));
+        plan->grid_ab32 = ctx->sm_count * (b > 0 ? b : 1);
+    }
     plan->grid_vec = ctx->sm_count * 4;
     return MBE_OK;
 }
 
-// Workspace bytes of large_setup (plus `extra`, and the dense Hs unless aliased).
-static size_t large_bytes(int norb, int n, int k, bool dense_separate)
+// Workspace bytes of large_setup (and the dense Hs unless aliased).
+static size_t large_bytes(int norb, int n, int k, bool dense_separate, bool fp32)
 {
     const int64_t ns = binom(n, k), N = ns * ns;
     const int P = n * (n + 1) / 2;
@@ -2575,22 +2782,33 @@ static size_t large_bytes(int norb, int n, int k, bool dense_separate)
                align256(P * 8) + align256(2 * P * 2) + align256((ns + 1) * 8) + align256(ns * conn * 4) +
                align256(ns * conn * 8) + align256(ns * conn * 4) + align256(N * 8) + align256(ns * 4) +
                align256((ns + 1) * 8) + 4096;
+    b += align256((size_t)k * (n - k + 1) * ns * 4) + align256((size_t)N * 8);
+    if (fp32) b += align256((size_t)P * large_nsp(ns) * 4);
     if (dense_separate) b += align256((size_t)ns * ns * 8);
     return b;
 }
 
+// sigma = H c: the opposite-spin term written first, then Hs C added, then C Hs^T
+// added through the transposed copy of c.
 template <typename T>
 static int large_sigma_launch(mbe_ctx *ctx, const LargePlan &pl, const T *c, double *sigma, int order_tag)
 {
     TimedLaunch tl(ctx, order_tag, 2, sizeof(T) == 8 ? 64 : 32);
-    if (sizeof(T) == 8)
-        k_large_sigma<double><<<pl.grid_sigma64, SIGMA_THREADS, pl.smem64, ctx->stream>>>(pl.L, (const double *)c,
-                                                                                          sigma);
-    else
-        k_large_sigma<float><<<pl.grid_sigma32, SIGMA_THREADS, pl.smem32, ctx->stream>>>(pl.L, (const float *)c,
-                                                                                         sigma);
+    const int Ns = pl.L.Ns;
+    T *cT = (T *)pl.cT;
+    if (sizeof(T) == 8) {
+        k_large_ab64<<<pl.grid_ab64, SIGMA_THREADS, pl.smem_ab64, ctx->stream>>>(pl.L, (const double *)c, sigma);
+    } else {
+        k_large_ab32<<<pl.grid_ab32, pl.ab32_threads, pl.smem_ab32, ctx->stream>>>(pl.L, pl.Pp, pl.Nsp,
+                                                                                  (const float *)c, pl.inv, sigma);
+    }
+    const int grid_ss = sizeof(T) == 8 ? pl.grid_ss64 : pl.grid_ss32;
+    const size_t smem_ss = sizeof(T) == 8 ? pl.smem_ss64 : pl.smem_ss32;
+    k_large_ss<T, false><<<grid_ss, SS_THREADS, smem_ss, ctx->stream>>>(pl.L, c, sigma);
+    k_large_transpose<T><<<pl.grid_tr, dim3(32, 8), 0, ctx->stream>>>(c, Ns, cT);
+    k_large_ss<T, true><<<grid_ss, SS_THREADS, smem_ss, ctx->stream>>>(pl.L, cT, sigma);
     MBE_CU(cudaGetLastError());
-    ++ctx->launches;
+    ctx->launches += 4;
     return tl.done();
 }
 
@@ -2614,7 +2832,8 @@ extern "C" int casci_sigma_large(mbe_ctx *ctx, int norb, const double *h1, const
     int k0 = 0;
     for (int i = 0; i < n_cas; ++i) k0 += (cas_orbs[i] >= 0 && cas_orbs[i] < norb && occ_h[cas_orbs[i]]) ? 1 : 0;
     const int64_t N = binom(n_cas, k0) * binom(n_cas, k0);
-    size_t bytes = large_bytes(norb, n_cas, k0, true) + (precision == MBE_PREC_MIXED ? align256(N * 4) : 0);
+    const bool fp32 = precision == MBE_PREC_MIXED;
+    size_t bytes = large_bytes(norb, n_cas, k0, true, fp32) + (fp32 ? align256(N * 4) : 0);
     void *ws = nullptr;
     int rc = workspace(ctx, bytes, &ws);
     if (rc) return rc;
@@ -2622,7 +2841,7 @@ extern "C" int casci_sigma_large(mbe_ctx *ctx, int norb, const double *h1, const
     LargePlan pl;
     int k = 0;
     int64_t dphi = 0;
-    rc = large_setup(ctx, norb, h1, eri, occ, n_cas, cas_orbs, bump, nullptr, &pl, &k, &dphi);
+    rc = large_setup(ctx, norb, h1, eri, occ, n_cas, cas_orbs, bump, nullptr, fp32, &pl, &k, &dphi);
     if (rc) return rc;
     if (diag) MBE_CU(cudaMemcpyAsync(diag, pl.L.diag, N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
     if (precision == MBE_PREC_FP64) return large_sigma_launch<double>(ctx, pl, c, sigma, n_cas);
@@ -2808,7 +3027,8 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
     LargeDav D;
     D.ld = vec / 8;
     D.nblk = ctx->sm_count * 4;
-    size_t bytes = large_bytes(norb, n_cas, k0, false) + vec * (2 * MLARGE + 5) + align256((size_t)N * 4) +
+    const bool mixed = o.precision == MBE_PREC_MIXED;
+    size_t bytes = large_bytes(norb, n_cas, k0, false, mixed) + vec * (2 * MLARGE + 5) + align256((size_t)N * 4) +
                    align256((size_t)D.nblk * LRED * 8) + 8 * 256 + 4096;
     void *ws = nullptr;
     int rc = workspace(ctx, bytes, &ws);
@@ -2833,14 +3053,13 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
     int k = 0;
     int64_t dphi = 0;
     // The dense one-spin Hamiltonian of the set-up lives in the (not yet used) basis region.
-    rc = large_setup(ctx, norb, h1, eri, occ, n_cas, cas_orbs, bump, D.V, &pl, &k, &dphi);
+    rc = large_setup(ctx, norb, h1, eri, occ, n_cas, cas_orbs, bump, D.V, mixed, &pl, &k, &dphi);
     if (rc) return rc;
     k_argmin<<<1, 1024, 0, ctx->stream>>>(pl.L.diag, N, D.best);
     k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best, N, D.x);
     ctx->launches += 2;
     double lam = 0.0, rn = 0.0;
     int n32 = 0, n64 = 0, st32 = 0, st = 0;
-    const bool mixed = o.precision == MBE_PREC_MIXED;
     if (mixed) {
         rc = large_phase<float>(ctx, pl, D, o.tol_switch, 0, o.max_iter, true, &lam, &rn, &n32, &st32);
         if (rc) return rc;

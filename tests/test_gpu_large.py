@@ -59,7 +59,12 @@ def test_large_sigma_matches_casci_sigma(eng, ctx, A):
     assert np.abs(g32.cpu().numpy() - w).max() <= 2e-5 * np.abs(w).max()
 
 
-def test_large_sigma_14_orbitals_sampled_rows(eng, ctx, molecule):
+# float32 arithmetic: relative error of a sum of ~10^3 products of unit-scale terms
+TOL_REL = {"fp64": 1e-11, "mixed": 2e-5}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_large_sigma_14_orbitals_sampled_rows(eng, ctx, molecule, prec):
     h1, eri, occ = molecule
     A = list(range(1, 15))  # (14e,14o): 11,778,624 determinants
     k = omb.n_active_electrons(occ, A)
@@ -67,12 +72,31 @@ def test_large_sigma_14_orbitals_sampled_rows(eng, ctx, molecule):
     assert N == 11_778_624
     rng = np.random.default_rng(14)
     c = rng.normal(size=N)
-    got, _ = ctx.casci_sigma_large(dev(h1), dev(eri), dev(occ), A, dev(c), "fp64")
+    got, _ = ctx.casci_sigma_large(dev(h1), dev(eri), dev(occ), A, dev(c), prec)
     got = got.cpu().numpy()
     _, h_eff, eri_a = omb.frozen_core(h1, eri, occ, A)
     rows = rng.choice(N, size=60, replace=False)
     want = fci.sigma_rows(h_eff, eri_a, k, k, c, rows)
-    assert np.abs(got[rows] - want).max() <= 1e-11 * np.abs(want).max()
+    assert np.abs(got[rows] - want).max() <= TOL_REL[prec] * np.abs(want).max()
+
+
+def test_large_sigma_16_orbitals_sampled_rows(eng, ctx, molecule):
+    h1, eri, occ = molecule
+    A = list(range(16))  # (16e,16o): 165,636,900 determinants
+    k = omb.n_active_electrons(occ, A)
+    N = math.comb(16, k) ** 2
+    assert N == 165_636_900
+    g = torch.Generator(device="cuda")
+    g.manual_seed(16)
+    c = torch.randn(N, dtype=torch.float64, device="cuda", generator=g)
+    c_host = c.cpu().numpy()
+    _, h_eff, eri_a = omb.frozen_core(h1, eri, occ, A)
+    rows = np.random.default_rng(16).choice(N, size=40, replace=False)
+    want = fci.sigma_rows(h_eff, eri_a, k, k, c_host, rows)
+    for prec in ("fp64", "mixed"):
+        got = ctx.casci_sigma_large(dev(h1), dev(eri), dev(occ), A, c, prec)[0]
+        got = got[torch.as_tensor(rows, device="cuda")].cpu().numpy()
+        assert np.abs(got - want).max() <= TOL_REL[prec] * np.abs(want).max(), prec
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
