@@ -130,4 +130,27 @@ struct Bump {
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Position of the m-tuple `key` in a lexicographically sorted list, or -1.
+__device__ inline int64_t find_tuple(const int32_t *list, int64_t len, int m, const int32_t *key)
+{
+    int64_t lo = 0, hi = len - 1;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) >> 1;
+        const int32_t *row = list + mid * m;
+        int cmp = 0;
+        for (int i = 0; i < m; ++i) {
+            if (row[i] != key[i]) {
+                cmp = row[i] < key[i] ? -1 : 1;
+                break;
+            }
+        }
+        if (cmp == 0) return mid;
+        if (cmp < 0) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+// Exclusive scan of per-block counts into offsets[0..nblocks] (one block).
+__global__ void k_scan_counts(const int32_t *counts, int64_t nblocks, int64_t *offsets);
+
 }  // namespace mbe

@@ -14,26 +14,6 @@ struct LowerLists {
     int64_t count[MBE_MAX_ORDER];
 };
 
-// Position of the m-tuple `key` in a lexicographically sorted list, or -1.
-__device__ inline int64_t find_tuple(const int32_t *list, int64_t len, int m, const int32_t *key)
-{
-    int64_t lo = 0, hi = len - 1;
-    while (lo <= hi) {
-        int64_t mid = (lo + hi) >> 1;
-        const int32_t *row = list + mid * m;
-        int cmp = 0;
-        for (int i = 0; i < m; ++i) {
-            if (row[i] != key[i]) {
-                cmp = row[i] < key[i] ? -1 : 1;
-                break;
-            }
-        }
-        if (cmp == 0) return mid;
-        if (cmp < 0) lo = mid + 1; else hi = mid - 1;
-    }
-    return -1;
-}
-
 // One thread per tuple: Delta eps = eps - sum over the proper subsets (bit masks
 // 1 .. 2^order - 2 of the tuple's positions, in that order) of their increments.
 __global__ void k_increments(int order, int64_t n_tuples, const int32_t *tuples, const double *eps,
