@@ -341,6 +341,39 @@ int casci_sigma_large(mbe_ctx *ctx, int norb, const double *h1, const double *er
 int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ, int n_cas,
                 const int32_t *cas_orbs, const mbe_opts *opts, double *result, int32_t *info, double *cvec);
 
+/* ------------------------------------------------------------------ screened expansion */
+
+/*
+ * Child spawning of the screened expansion (Sec. 2: children at order k+1 are
+ * spawned from the order-k tuples; thresholds by Eq. 4).  An order-(order+1)
+ * tuple of the expansion space is listed when
+ *     max over its order-`order` sub-tuples S of |Delta eps(S)|  >  T_tup(child),
+ *     T_tup = 0 if M_tup < m_init, else t_init * a^(M_tup - m_init) (repeated
+ *     products), M_tup = max(occupied, virtual orbitals of the child),
+ * a sub-tuple missing from `parents` counting as zero, and the child kept by the
+ * skip rule when MBE_SKIP_NO_OCC_OR_VIRT is set.  Output in lexicographic order.
+ *   occ [norb], exp_orbs [n_exp], ref_orbs [n_ref]   host, as for mbe_tuples
+ *   order                                            parent order k (1 <= k, k+1 <= n_exp)
+ *   parents [n_parents*order], parent_incs [n_parents]
+ *                                                    device: the computed order-k
+ *                                                    tuples (lexicographic, as listed
+ *                                                    by mbe_tuples or mbe_screen) and
+ *                                                    their increments
+ *   capacity                                         rows available in `children`
+ *   n_children                                       host out: number of children
+ *   children [capacity*(order+1)]                    device out, or NULL to count only
+ * The call synchronises the context stream once (to read the count); with
+ * children != NULL the children are then written asynchronously.  A count
+ * query and the writing call run the same selection.
+ * Errors: MBE_EINVAL (bad indices or orders, negative thresholds, count above
+ * capacity), MBE_EUNSUPPORTED (more than 2^31 x 256 candidates), MBE_ENOMEM,
+ * MBE_ECUDA.
+ */
+int mbe_screen(mbe_ctx *ctx, int norb, const uint8_t *occ, int n_exp, const int32_t *exp_orbs, int n_ref,
+               const int32_t *ref_orbs, int order, int64_t n_parents, const int32_t *parents,
+               const double *parent_incs, double t_init, int m_init, double a, int flags, int64_t capacity,
+               int64_t *n_children, int32_t *children);
+
 /* ------------------------------------------------------------------ a8-a9: Eqs. 2, 1 */
 
 /*

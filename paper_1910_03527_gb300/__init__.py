@@ -18,5 +18,6 @@ from .binding import (  # noqa: F401
     library_path,
     mbe_gradient,
     run_mbe,
+    run_mbe_screened,
 )
 from ._build import build  # noqa: F401

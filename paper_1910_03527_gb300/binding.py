@@ -30,7 +30,8 @@ EXPORTS = ("mbe_default_opts", "mbe_ctx_create", "mbe_ctx_set_stream", "mbe_ctx_
            "mbe_last_error", "mbe_ctx_sync", "mbe_ctx_launches", "mbe_ctx_set_timing",
            "mbe_ctx_timings", "mbe_tuples", "mbe_string_table", "mbe_phi_energy",
            "casci_batch", "casci_sigma", "casci_sigma_noalloc", "mbe_increments", "mbe_total",
-           "mbe_weights", "casci_rdm_batch", "mbe_phi_gradient", "casci_sigma_large", "casci_solve")
+           "mbe_weights", "casci_rdm_batch", "mbe_phi_gradient", "casci_sigma_large", "casci_solve",
+           "mbe_screen")
 
 
 class MbeOpts(ctypes.Structure):
@@ -106,6 +107,9 @@ def lib() -> ctypes.CDLL:
     L.casci_sigma_large.argtypes = [P, i32, P, P, P, i32, P, i32, P, P, P]
     L.casci_solve.restype = i32
     L.casci_solve.argtypes = [P, i32, P, P, P, i32, P, ctypes.POINTER(MbeOpts), P, P, P]
+    L.mbe_screen.restype = i32
+    L.mbe_screen.argtypes = [P, i32, P, i32, P, i32, P, i32, i64, P, P, dbl, i32, dbl, i32, i64,
+                             ctypes.POINTER(i64), P]
     return L
 
 
@@ -219,6 +223,24 @@ class Context:
         if n.value > 0:
             _check(lib().mbe_tuples(self._h, norb, occ_h, len(exp), exp_h, len(ref), ref_h, order,
                                     flags, ctypes.byref(n), self._p(out)), "mbe_tuples")
+        return out
+
+    def mbe_screen(self, norb: int, occ: Sequence[int], exp: Sequence[int], ref: Sequence[int], order: int,
+                   parents: torch.Tensor, parent_incs: torch.Tensor, t_init: float, m_init: int, a: float,
+                   skip: bool) -> torch.Tensor:
+        """Order-(order+1) children spawned from the order-`order` tuples and increments."""
+        n = ctypes.c_int64()
+        flags = MBE_SKIP_NO_OCC_OR_VIRT if skip else 0
+        occ_h, exp_h, ref_h = _u8_host(occ), _i32_host(exp), _i32_host(ref)
+        n_par = int(parents.shape[0])
+        args = (self._h, norb, occ_h, len(exp), exp_h, len(ref), ref_h, order, n_par,
+                self._p(self._dev(parents, torch.int32, "parents")),
+                self._p(self._dev(parent_incs, torch.float64, "parent increments")),
+                float(t_init), int(m_init), float(a), flags)
+        _check(lib().mbe_screen(*args, 0, ctypes.byref(n), None), "mbe_screen(count)")
+        out = self._empty((n.value, order + 1), torch.int32)
+        if n.value > 0:
+            _check(lib().mbe_screen(*args, n.value, ctypes.byref(n), self._p(out)), "mbe_screen")
         return out
 
     def mbe_string_table(self, n_orb: int, n_el: int):
@@ -460,6 +482,46 @@ def run_mbe(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequence[int],
         out["status"].append(status)
         out["iters"].append(iters)
         out["inc"].append(inc)
+    e_order, e_total = ctx.mbe_total(out["inc"], e_phi, e_ref)
+    out["e_order"] = e_order
+    out["e_total"] = e_total
+    return out
+
+
+def run_mbe_screened(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequence[int], max_order: int,
+                     skip: bool, t_init: float = 1e-10, m_init: int = 3, a: float = 5.0,
+                     opts: Optional[Opts] = None, occ_host: Optional[Sequence[int]] = None):
+    """The screened expansion through the C ABI: orders up to the first computed
+    one (order 2 for an empty reference space with the skip rule, else 1) are
+    complete; every later order holds the children mbe_screen spawns from the
+    order below, until max_order or until no child is spawned.  Returns the
+    dict of run_mbe plus "orders" (the orders with tuples)."""
+    occ_h = [int(v) for v in (occ_host if occ_host is not None else occ.cpu().tolist())]
+    norb = h1.shape[0]
+    e_phi = ctx.mbe_phi_energy(h1, eri, occ)
+    e_ref = 0.0
+    if len(ref) > 0:
+        eps_r, st_r, _ = ctx.casci_batch(h1, eri, occ, ref, 0.0, 0, None, opts)
+        e_ref = float(eps_r.item())
+    k0 = 2 if (skip and len(ref) == 0) else 1
+    out = dict(tuples=[], eps=[], status=[], iters=[], inc=[], e_phi=e_phi, e_ref_corr=e_ref, orders=[])
+    for n in range(1, max_order + 1):
+        if n <= k0:
+            tup = ctx.mbe_tuples(norb, occ_h, exp, ref, n, skip)
+        else:
+            tup = ctx.mbe_screen(norb, occ_h, exp, ref, n - 1, out["tuples"][-1], out["inc"][-1],
+                                 t_init, m_init, a, skip)
+        if tup.shape[0] == 0 and n >= k0:
+            break
+        eps, status, iters = ctx.casci_batch(h1, eri, occ, ref, e_ref, n, tup, opts)
+        inc = ctx.mbe_increments(n, tup, eps, out["tuples"], out["inc"])
+        out["tuples"].append(tup)
+        out["eps"].append(eps)
+        out["status"].append(status)
+        out["iters"].append(iters)
+        out["inc"].append(inc)
+        if tup.shape[0] > 0:
+            out["orders"].append(n)
     e_order, e_total = ctx.mbe_total(out["inc"], e_phi, e_ref)
     out["e_order"] = e_order
     out["e_total"] = e_total

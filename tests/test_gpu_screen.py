@@ -1,0 +1,156 @@
+"""Parity of the device child spawning (mbe_screen) and of the screened expansion
+against the oracle.
+
+* Spawning from identical increments must select bit-identical child lists:
+  both sides compare the same float64 magnitudes with the same Eq. 4 thresholds
+  (formed by the same repeated products). Inputs: oracle increments of small
+  systems, and seeded synthetic increments on larger expansion spaces (log-
+  uniform magnitudes, exact zeros, randomly dropped parents) that span several
+  tiles of the count, sort and write kernels.
+* The screened expansion end to end: the tuple lists per order are compared
+  exactly on cases whose every spawning decision is at least 1e-5 E_h from its
+  threshold (checked here on the oracle's numbers), the energies within the
+  solver tolerance.
+"""
+
+import ctypes
+import itertools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import mbe as omb  # noqa: E402
+from workloads import random_system  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def eng():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1910_03527_gb300 as e
+    e.build()
+    return e
+
+
+@pytest.fixture(scope="module")
+def ctx(eng):
+    c = eng.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=None):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda", dtype=dtype)
+
+
+def gpu_spawn(ctx, occ, exp, ref, order, parents, incs, t_init, m_init, a, skip):
+    par = dev(np.array(parents, dtype=np.int32).reshape(len(parents), order), torch.int32)
+    inc = dev(np.array(incs, dtype=np.float64), torch.float64)
+    got = ctx.mbe_screen(len(occ), [int(v) for v in occ], exp, ref, order, par, inc, t_init, m_init, a, skip)
+    return [tuple(int(x) for x in row) for row in got.cpu().numpy()]
+
+
+@pytest.mark.parametrize("skip", [True, False])
+def test_spawn_from_oracle_increments(ctx, skip):
+    h1, eri, occ = random_system(8, 4, seed=41)
+    exp = list(range(8))
+    full = omb.run_mbe(h1, eri, occ, [], exp, [1, 2, 3], skip)
+    for order in (2, 3):
+        tups = omb.tuples(exp, [], occ, order, skip)
+        incs = [full["inc"][t] for t in tups]
+        mags = np.sort(np.abs(incs))
+        for t_init in (0.0, float(mags[len(mags) // 3]), float(mags[2 * len(mags) // 3])):
+            want = omb.spawn(exp, [], occ, order, dict(zip(tups, incs)), skip, t_init, 2, 3.0)
+            got = gpu_spawn(ctx, occ, exp, [], order, tups, incs, t_init, 2, 3.0, skip)
+            assert got == want, (order, t_init)
+
+
+def _synthetic(M, order, occ_mask, seed, drop):
+    rng = np.random.default_rng(seed)
+    exp = list(range(M))
+    tups = [t for t in itertools.combinations(exp, order)
+            if 0 < sum(occ_mask[p] for p in t) < order]
+    keep = rng.random(len(tups)) >= drop
+    tups = [t for t, k in zip(tups, keep) if k]
+    mags = 10.0 ** rng.uniform(-14, -2, size=len(tups))
+    mags[rng.random(len(tups)) < 0.05] = 0.0
+    incs = mags * rng.choice([-1.0, 1.0], size=len(tups))
+    return exp, tups, incs
+
+
+@pytest.mark.parametrize("M,order,nocc,drop,seed", [(22, 3, 11, 0.0, 1), (22, 4, 11, 0.3, 2),
+                                                     (30, 3, 8, 0.5, 3), (16, 5, 7, 0.2, 4)])
+def test_spawn_synthetic_increments(ctx, M, order, nocc, drop, seed):
+    occ = np.zeros(M, dtype=np.uint8)
+    occ[:nocc] = 1
+    exp, tups, incs = _synthetic(M, order, occ, seed, drop)
+    inc = dict(zip(tups, incs))
+    for t_init, m_init, a in ((1e-10, 3, 5.0), (1e-7, 2, 10.0), (0.0, 0, 1.0)):
+        want = omb.spawn(exp, [], occ, order, inc, True, t_init, m_init, a)
+        got = gpu_spawn(ctx, occ, exp, [], order, tups, incs, t_init, m_init, a, True)
+        assert len(got) == len(want)
+        assert got == want, (t_init, m_init, a)
+
+
+def test_spawn_edge_cases(eng, ctx):
+    from paper_1910_03527_gb300 import binding as b
+
+    occ = np.array([1, 1, 1, 0, 0, 0], dtype=np.uint8)
+    exp = list(range(6))
+    tups = omb.tuples(exp, [], occ, 2, True)
+    # no parents, all-zero increments, an unreachable threshold
+    assert gpu_spawn(ctx, occ, exp, [], 2, [], [], 0.0, 0, 1.0, True) == []
+    assert gpu_spawn(ctx, occ, exp, [], 2, tups, [0.0] * len(tups), 0.0, 0, 1.0, True) == []
+    assert gpu_spawn(ctx, occ, exp, [], 2, tups, [1.0] * len(tups), 1e10, 0, 1.0, True) == []
+    # zero threshold with non-zero increments: every kept child
+    got = gpu_spawn(ctx, occ, exp, [], 2, tups, [1e-3] * len(tups), 0.0, 0, 1.0, True)
+    assert got == omb.tuples(exp, [], occ, 3, True)
+    # a non-empty reference space satisfies the skip rule for every child
+    ref = [2, 3]
+    exp2 = [0, 1, 4, 5]
+    t1 = omb.tuples(exp2, ref, occ, 1, True)
+    got = gpu_spawn(ctx, occ, exp2, ref, 1, t1, [1e-3] * len(t1), 0.0, 0, 1.0, True)
+    assert got == omb.tuples(exp2, ref, occ, 2, True)
+    # a capacity below the count is an error, not a truncation
+    par = dev(np.array(tups, dtype=np.int32), torch.int32)
+    inc = dev(np.full(len(tups), 1e-3), torch.float64)
+    n = ctypes.c_int64()
+    out = torch.empty((4, 3), dtype=torch.int32, device="cuda")
+    with pytest.raises(eng.MbeError):
+        b._check(b.lib().mbe_screen(ctx._h, 6, b._u8_host(occ), 6, b._i32_host(exp), 0, b._i32_host([]), 2,
+                                    len(tups), ctx._p(par), ctx._p(inc), 0.0, 0, 1.0, 1, 4, ctypes.byref(n),
+                                    ctx._p(out)), "mbe_screen")
+
+
+@pytest.mark.parametrize("case", [(33, 8, 4, 3e-3, 2, 3.0, 7), (35, 8, 3, 2e-3, 2, 2.0, 6)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_screened_expansion_matches_oracle(eng, ctx, case, prec):
+    seed, n, nocc, t_init, m_init, a, max_order = case
+    h1, eri, occ = random_system(n, nocc, seed=seed)
+    exp = list(range(n))
+    want = omb.run_mbe_screened(h1, eri, occ, [], exp, max_order, True, t_init=t_init, m_init=m_init, a=a)
+    # every spawning decision of the oracle run is far from its threshold
+    for k in want["orders"]:
+        inc = {t: want["inc"][t] for t in want["tuples"][k]}
+        for child in itertools.combinations(exp, k + 1):
+            if not omb.keep_tuple(child, [], occ):
+                continue
+            best = max(abs(inc.get(s, 0.0)) for s in itertools.combinations(child, k))
+            thr = omb.tuple_threshold(child, occ, t_init, m_init, a)
+            assert best == 0.0 or abs(best - thr) > 1e-5
+    got = eng.run_mbe_screened(ctx, dev(h1), dev(eri), dev(occ), [], exp, max_order, True, t_init=t_init,
+                               m_init=m_init, a=a, opts=eng.Opts(precision=prec), occ_host=occ.tolist())
+    assert got["orders"] == want["orders"]
+    tol = 1e-9 if prec == "fp64" else 1e-8
+    for k in want["orders"]:
+        tk = [tuple(int(x) for x in r) for r in got["tuples"][k - 1].cpu().numpy()]
+        assert tk == want["tuples"][k]
+        gi = got["inc"][k - 1].cpu().numpy()
+        wi = np.array([want["inc"][t] for t in tk])
+        assert np.abs(gi - wi).max() <= tol
+        assert int((got["status"][k - 1] != 0).sum()) == 0
+    assert abs(float(got["e_total"].item()) - want["e_tot"]) <= 10 * tol
