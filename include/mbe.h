@@ -329,9 +329,11 @@ int casci_sigma_large(mbe_ctx *ctx, int norb, const double *h1, const double *er
 /*
  * Lowest eigenpair of one large active space (a6 for a single big CASCI): the
  * Davidson of casci_batch (12-vector basis, thick restart on the two lowest
- * Ritz vectors, float32 then float64 phase in mixed mode) with every vector
- * operation in grid-wide kernels and the projected eigenproblem solved by one
- * warp on the device.  Synchronous: the host reads one residual norm per
+ * Ritz vectors) with every vector operation in grid-wide kernels and the
+ * projected eigenproblem solved by one warp on the device; float32 then
+ * float64 phase in mixed mode, as in casci_batch.  Both spin-flip sectors
+ * (alpha and beta strings exchanged, P c = +c and P c = -c) are solved and the
+ * lower eigenvalue kept.  Synchronous: the host reads one residual norm per
  * iteration.
  *   result [3]  host out: lambda, eps = lambda - <Phi_A|H_A|Phi_A>, residual norm
  *   info [3]    host out: status (MBE_STATUS_*), float64 sigma products, float32 ones

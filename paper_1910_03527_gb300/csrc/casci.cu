@@ -135,7 +135,28 @@ struct Problem {
     double *diag;         // [N]
     void *c;              // [N] vector sigma reads (T)
     void *sbuf;           // [N] sigma output staging (warp solver)
+    int sector;           // spin-flip sector of the solver's vectors (+1 or -1)
 };
+
+// Symmetric counterpart of determinant d = Ia * Ns + Ib under the exchange of the
+// alpha and beta strings.
+__device__ inline int flip_det(int d, int Ns)
+{
+    const int ia = d / Ns;
+    return (d - ia * Ns) * Ns + ia;
+}
+
+// Advances (ia, ib) by `step` positions through the row-major upper triangle
+// ia <= ib < Ns; past the end, ia reaches Ns.
+__device__ inline void tri_advance(int &ia, int &ib, int step, int Ns)
+{
+    int r = ib - ia + step;
+    while (ia < Ns && r >= Ns - ia) {
+        r -= Ns - ia;
+        ++ia;
+    }
+    ib = ia + r;
+}
 
 __host__ __device__ inline int odd_stride(int x) { return x | 1; }
 
@@ -550,11 +571,24 @@ __device__ void rdm_flush(const BatchArgs &a, const Problem &pb, const double *g
 template <typename T, int DPL>
 __device__ inline void sigma_warp(const Problem &pb, const T *V, const T *Hs, const T *c, T *sbuf, T (&out)[DPL])
 {
-    const int lane = threadIdx.x & 31;
-    // One compact loop (not unrolled DPL times) keeps the kernel small enough for
-    // the instruction cache; each lane reads back only the elements it wrote.
+    const int lane = threadIdx.x & 31, Ns = pb.Ns;
+    // c lies in one spin-flip sector (P c = sector * c) and H commutes with P, so
+    // only the elements with Ia <= Ib are computed and the others mirrored,
+    // sigma[P d] = sector * sigma[d]; the diagonal of the odd sector vanishes.
+    // One compact loop (not unrolled) keeps the kernel small for the
+    // instruction cache.
+    const int nh = Ns * (Ns + 1) / 2;
+    int ia = 0, ib = 0;
+    tri_advance(ia, ib, lane, Ns);
 #pragma unroll 1
-    for (int d = lane; d < pb.N; d += 32) sbuf[d] = sigma_elem<T>(pb, V, Hs, c, d);
+    for (int h = lane; h < nh; h += 32) {
+        const int d = ia * Ns + ib, pd = ib * Ns + ia;
+        const T v = (pb.sector < 0 && ia == ib) ? (T)0 : sigma_elem<T>(pb, V, Hs, c, d);
+        sbuf[d] = v;
+        if (pd != d) sbuf[pd] = pb.sector > 0 ? v : -v;
+        tri_advance(ia, ib, 32, Ns);
+    }
+    __syncwarp();
 #pragma unroll
     for (int j = 0; j < DPL; ++j) {
         int d = lane + 32 * j;
@@ -617,7 +651,8 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
             if (d < pb.N) {
                 T r = hx[j] - lam * x[j];
                 rr += r * r;
-                T den = (T)pb.diag[d] - lam;
+                const int pd = flip_det(d, pb.Ns);
+                T den = (T)pb.diag[d < pd ? d : pd] - lam;
                 if (fabs(den) < (T)1e-4) den = den >= (T)0 ? (T)1e-4 : (T)-1e-4;
                 c[d] = r / den;
             }
@@ -746,12 +781,12 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
 
 struct WarpLayout {
     int off_A, off_pp, off_h, off_hp, off_V64, off_V32, off_Hs64, off_Hs32, off_diag, off_c, off_s, off_str,
-        off_tab, off_g1, bytes;
+        off_tab, off_g1, off_x2, bytes;
 };
 
 __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline WarpLayout warp_layout(int n, int ns, int r, int N)
+__host__ __device__ inline WarpLayout warp_layout(int n, int ns, int r, int N, bool keep_vector)
 {
     WarpLayout L;
     int P = n * (n + 1) / 2, HSS = odd_stride(ns), RS = odd_stride(r > 0 ? r : 1);
@@ -770,9 +805,36 @@ __host__ __device__ inline WarpLayout warp_layout(int n, int ns, int r, int N)
     L.off_str = o; o = al16(o + 4 * ns);
     L.off_tab = o; o = al16(o + 4 * ns * RS);
     L.off_g1 = o; o = al16(o + 8 * n * n);
+    L.off_x2 = o; o = al16(o + (keep_vector ? 8 * N : 0));
     L.bytes = o;
     return L;
 }
+
+// Spin-flip symmetry. Exchanging the alpha and beta strings, (P c)[Ia][Ib] =
+// c[Ib][Ia], commutes with H (the sigma is symmetric in the two spins), so H is
+// block-diagonal in the sectors P c = +c (holding the closed-shell determinants)
+// and P c = -c. Each sector is solved from its own start vector, and the lower
+// of the two lowest eigenvalues is the lowest of the determinant space.
+struct SectorGuess {
+    int g;    // determinant of the start vector
+    int sgn;  // sector: +1 or -1
+};
+
+// Start-vector element d of a sector: e_g + sgn e_{P g}, plus a fixed admixture
+// that has the sector's symmetry.
+__device__ inline double sector_guess(int d, int Ns, SectorGuess sg)
+{
+    const int ia = d / Ns, ib = d - ia * Ns;
+    const int pd = ib * Ns + ia, pg = (sg.g % Ns) * Ns + sg.g / Ns;
+    double v = (d == sg.g ? 1.0 : 0.0) + (d == pg ? (double)sg.sgn : 0.0);
+    const double z = GUESS_NOISE * guess_noise(d < pd ? d : pd);
+    if (d == pd) return sg.sgn > 0 ? v + z : v;
+    return v + (d < pd ? z : sg.sgn * z);
+}
+
+// The float32 eigenvalue of the second sector must lie below the first sector's
+// eigenvalue by more than this float32 rounding margin to be refined in float64.
+__host__ __device__ inline double sector_margin(double lam) { return 1e-5 * (1.0 + fabs(lam)); }
 
 __device__ inline void store_result(const BatchArgs &a, int64_t t, double eps, int status, int n64, int n32)
 {
@@ -846,14 +908,20 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
             __syncwarp();
             continue;
         }
-        // start vector: lowest diagonal element (ties -> lowest index) + fixed admixture
-        double best = 1e300;
-        int bi = 0x7fffffff;
+        // start vectors: the lowest diagonal element (ties -> lowest index), and for
+        // the P = -1 sector the lowest one with Ia != Ib
+        double best = 1e300, best_o = 1e300;
+        int bi = 0x7fffffff, bj = 0x7fffffff;
         for (int d = lane; d < pb.N; d += 32) {
-            double v = pb.diag[d];
+            const double v = pb.diag[d];
             if (v < best || (v == best && d < bi)) {
                 best = v;
                 bi = d;
+            }
+            const int ia = d / pb.Ns;
+            if (ia != d - ia * pb.Ns && (v < best_o || (v == best_o && d < bj))) {
+                best_o = v;
+                bj = d;
             }
         }
 #pragma unroll
@@ -864,29 +932,78 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
                 best = ov;
                 bi = oi;
             }
+            ov = __shfl_xor_sync(FULL, best_o, o);
+            oi = __shfl_xor_sync(FULL, bj, o);
+            if (ov < best_o || (ov == best_o && oi < bj)) {
+                best_o = ov;
+                bj = oi;
+            }
         }
         double x64[DPL];
+        double *x2 = (double *)(ws + L.off_x2);
+        double lam = 0.0;
+        int status = MBE_STATUS_OK, n64 = 0, n32 = 0;
+        for (int sector = 0; sector < 2; ++sector) {
+            if (sector == 1 && (pb.Ns < 2 || status != MBE_STATUS_OK)) break;
+            const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
+            if (sector == 1 && a.rdm) {
 #pragma unroll
-        for (int j = 0; j < DPL; ++j) {
-            int d = lane + 32 * j;
-            x64[j] = (d < pb.N) ? ((d == bi ? 1.0 : 0.0) + GUESS_NOISE * guess_noise(d)) : 0.0;
+                for (int j = 0; j < DPL; ++j) {
+                    const int d = lane + 32 * j;
+                    if (d < pb.N) x2[d] = x64[j];
+                }
+            }
+            pb.sector = sg.sgn;
+#pragma unroll
+            for (int j = 0; j < DPL; ++j) {
+                const int d = lane + 32 * j;
+                x64[j] = (d < pb.N) ? sector_guess(d, pb.Ns, sg) : 0.0;
+            }
+            // the second sector is refined in float64 only if its float32
+            // eigenvalue may lie below the first sector's
+            bool lose = false;
+            if (mixed) {
+                float x32[DPL];
+#pragma unroll
+                for (int j = 0; j < DPL; ++j) x32[j] = (float)x64[j];
+                PhaseOut o32 = davidson_warp<float, DPL>(pb, x32, a.tol_switch, 0, a.max_iter, true);
+                n32 += o32.nsig;
+                // (only a converged float32 eigenvalue decides; a stalled phase goes on in float64)
+                if (sector == 1)
+                    lose = o32.status == MBE_STATUS_NONFINITE ||
+                           (o32.rnorm <= a.tol_switch && o32.lambda > lam + sector_margin(lam));
+                if (o32.status != MBE_STATUS_NONFINITE && !lose)
+#pragma unroll
+                    for (int j = 0; j < DPL; ++j) x64[j] = (double)x32[j];
+            }
+            if (!lose) {
+                PhaseOut o64 = davidson_warp<double, DPL>(pb, x64, a.tol, mixed ? a.min_fp64 : 0, a.max_iter, false);
+                n64 += o64.nsig;
+                if (sector == 0) {
+                    lam = o64.lambda;
+                    status = o64.status;
+                } else {
+                    lose = o64.status == MBE_STATUS_NONFINITE || !(o64.lambda < lam);
+                    if (!lose) {
+                        lam = o64.lambda;
+                        status = o64.status;
+                    }
+                }
+            }
+            if (lose && a.rdm) {
+                __syncwarp();
+#pragma unroll
+                for (int j = 0; j < DPL; ++j) {
+                    const int d = lane + 32 * j;
+                    x64[j] = (d < pb.N) ? x2[d] : 0.0;
+                }
+            }
+            __syncwarp();
         }
-        int n32 = 0;
-        if (mixed) {
-            float x32[DPL];
-#pragma unroll
-            for (int j = 0; j < DPL; ++j) x32[j] = (float)x64[j];
-            PhaseOut o32 = davidson_warp<float, DPL>(pb, x32, a.tol_switch, 0, a.max_iter, true);
-            n32 = o32.nsig;
-            if (o32.status != MBE_STATUS_NONFINITE)
-#pragma unroll
-                for (int j = 0; j < DPL; ++j) x64[j] = (double)x32[j];
-        }
-        PhaseOut o64 = davidson_warp<double, DPL>(pb, x64, a.tol, mixed ? a.min_fp64 : 0, a.max_iter, false);
         if (lane == 0) {
-            double e = o64.status == MBE_STATUS_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL)
-                                                         : o64.lambda - ephi - a.e_ref_corr;
-            store_result(a, t, e, o64.status, o64.nsig, n32);
+            double e = status == MBE_STATUS_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL)
+                                                      : lam - ephi - a.e_ref_corr;
+            store_result(a, t, e, status, n64, n32);
         }
         __syncwarp();
         if (a.rdm) {
@@ -915,7 +1032,7 @@ constexpr int KRED = 16;  // values per block reduction (>= MMAX + 1)
 // Per-block workspace slot: the Davidson basis V, its image W = H V, the Ritz
 // vector x and H x, a spare correction vector, the diagonal and Hs.
 struct SlotLayout {
-    size_t off_V, off_W, off_x, off_hx, off_t, off_diag, off_Hs64, off_Hs32, vec, bytes;
+    size_t off_V, off_W, off_x, off_hx, off_t, off_diag, off_Hs64, off_Hs32, off_x2, vec, bytes;
 };
 
 __host__ __device__ inline SlotLayout slot_layout(int ns, int N)
@@ -933,6 +1050,7 @@ __host__ __device__ inline SlotLayout slot_layout(int ns, int N)
     L.off_diag = o; o += vec;
     L.off_Hs64 = o; o += ((size_t)ns * HSS * 8 + 255) & ~(size_t)255;
     L.off_Hs32 = o; o += ((size_t)ns * HSS * 4 + 255) & ~(size_t)255;
+    L.off_x2 = o; o += vec;
     L.bytes = o;
     return L;
 }
@@ -1124,6 +1242,24 @@ __device__ void small_eig_warp(const double *G, int m, float *A, float *E, float
 
 // One Davidson phase in precision T (block solver).  x: start vector in, Ritz
 // vector out.  V, W: MMAX vectors each, leading dimension ld (elements).
+// Block-wide sigma of a vector of one spin-flip sector: the elements with
+// Ia <= Ib are computed and mirrored (see sigma_warp); ends with a barrier.
+template <typename T>
+__device__ inline void sigma_block(const Problem &pb, const T *Vi, const T *Hs, const T *src, T *dst)
+{
+    const int Ns = pb.Ns, nh = Ns * (Ns + 1) / 2;
+    int ia = 0, ib = 0;
+    tri_advance(ia, ib, threadIdx.x, Ns);
+    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+        const int d = ia * Ns + ib, pd = ib * Ns + ia;
+        const T v = (pb.sector < 0 && ia == ib) ? (T)0 : sigma_elem<T>(pb, Vi, Hs, src, d);
+        dst[d] = v;
+        if (pd != d) dst[pd] = pb.sector > 0 ? v : -v;
+        tri_advance(ia, ib, blockDim.x, Ns);
+    }
+    __syncthreads();
+}
+
 template <typename T>
 __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *x, T *hx, T *tx, char *smem,
                                    const BlockSmem &S, double tol, int min_iter, int max_iter, bool steer)
@@ -1152,7 +1288,7 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
         for (int d = tid; d < N; d += nt) V[d] = x[d] * inv;
     }
     __syncthreads();
-    for (int d = tid; d < N; d += nt) W[d] = sigma_elem<T>(pb, Vi, Hs, V, d);
+    sigma_block<T>(pb, Vi, Hs, V, W);
     ++o.nsig;
     v[0] = 0;
     for (int d = tid; d < N; d += nt) v[0] += V[d] * W[d];
@@ -1183,7 +1319,8 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
             hx[d] = hs;
             T r = hs - th * xs;
             v[0] += r * r;
-            T den = (T)pb.diag[d] - th;
+            const int pd = flip_det(d, pb.Ns);
+            T den = (T)pb.diag[d < pd ? d : pd] - th;
             if (fabs(den) < (T)1e-4) den = den >= (T)0 ? (T)1e-4 : (T)-1e-4;
             const T td = r / den;
             tdst[d] = td;
@@ -1299,7 +1436,7 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
         for (int d = tid; d < N; d += nt) tv[d] *= tinv;
         __syncthreads();
         T *wv = W + (size_t)m * ld;
-        for (int d = tid; d < N; d += nt) wv[d] = sigma_elem<T>(pb, Vi, Hs, tv, d);
+        sigma_block<T>(pb, Vi, Hs, tv, wv);
         ++o.nsig;
 #pragma unroll
         for (int i = 0; i < KRED; ++i) v[i] = 0;
@@ -1377,14 +1514,20 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
             __syncthreads();
             continue;
         }
-        // argmin of the diagonal (ties -> lowest index)
-        double best = 1e300;
-        int bi = 0x7fffffff;
+        // start vectors: the lowest diagonal element (ties -> lowest index), and for
+        // the P = -1 sector the lowest one with Ia != Ib
+        double best = 1e300, best_o = 1e300;
+        int bi = 0x7fffffff, bj = 0x7fffffff;
         for (int d = threadIdx.x; d < pb.N; d += blockDim.x) {
-            double v = pb.diag[d];
+            const double v = pb.diag[d];
             if (v < best || (v == best && d < bi)) {
                 best = v;
                 bi = d;
+            }
+            const int ia = d / pb.Ns;
+            if (ia != d - ia * pb.Ns && (v < best_o || (v == best_o && d < bj))) {
+                best_o = v;
+                bj = d;
             }
         }
 #pragma unroll
@@ -1395,65 +1538,112 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
                 best = ov;
                 bi = oi;
             }
+            ov = __shfl_xor_sync(FULL, best_o, o);
+            oi = __shfl_xor_sync(FULL, bj, o);
+            if (ov < best_o || (ov == best_o && oi < bj)) {
+                best_o = ov;
+                bj = oi;
+            }
         }
         if ((threadIdx.x & 31) == 0) {
             red[threadIdx.x >> 5] = best;
-            ((int *)(red + 32))[threadIdx.x >> 5] = bi;
+            red[32 + (threadIdx.x >> 5)] = best_o;
+            ((int *)(red + 64))[threadIdx.x >> 5] = bi;
+            ((int *)(red + 64))[32 + (threadIdx.x >> 5)] = bj;
         }
         __syncthreads();
         best = red[0];
-        bi = ((int *)(red + 32))[0];
+        best_o = red[32];
+        bi = ((int *)(red + 64))[0];
+        bj = ((int *)(red + 64))[32];
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
             double ov = red[w];
-            int oi = ((int *)(red + 32))[w];
+            int oi = ((int *)(red + 64))[w];
             if (ov < best || (ov == best && oi < bi)) {
                 best = ov;
                 bi = oi;
             }
+            ov = red[32 + w];
+            oi = ((int *)(red + 64))[32 + w];
+            if (ov < best_o || (ov == best_o && oi < bj)) {
+                best_o = ov;
+                bj = oi;
+            }
         }
         __syncthreads();
         double *x64 = (double *)(slot + L.off_x);
-        for (int d = threadIdx.x; d < pb.N; d += blockDim.x)
-            x64[d] = (d == bi ? 1.0 : 0.0) + GUESS_NOISE * guess_noise(d);
-        __syncthreads();
-        int n32 = 0;
-        if (mixed) {
-            float *x32 = (float *)(slot + L.off_x);
-            // narrow x in place (float view of the same region), bottom up
-            for (int base = 0; base < pb.N; base += blockDim.x) {
-                int d = base + threadIdx.x;
-                double v = (d < pb.N) ? x64[d] : 0.0;
-                __syncthreads();
-                if (d < pb.N) x32[d] = (float)v;
-                __syncthreads();
+        double *x2 = (double *)(slot + L.off_x2);
+        double lam = 0.0;
+        int status = MBE_STATUS_OK, n64 = 0, n32 = 0;
+        for (int sector = 0; sector < 2; ++sector) {
+            if (sector == 1 && (pb.Ns < 2 || status != MBE_STATUS_OK)) break;
+            const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
+            if (sector == 1 && a.rdm)
+                for (int d = threadIdx.x; d < pb.N; d += blockDim.x) x2[d] = x64[d];
+            pb.sector = sg.sgn;
+            for (int d = threadIdx.x; d < pb.N; d += blockDim.x) x64[d] = sector_guess(d, pb.Ns, sg);
+            __syncthreads();
+            bool lose = false;
+            if (mixed) {
+                float *x32 = (float *)(slot + L.off_x);
+                // narrow x in place (float view of the same region), bottom up
+                for (int base = 0; base < pb.N; base += blockDim.x) {
+                    int d = base + threadIdx.x;
+                    double v = (d < pb.N) ? x64[d] : 0.0;
+                    __syncthreads();
+                    if (d < pb.N) x32[d] = (float)v;
+                    __syncthreads();
+                }
+                PhaseOut o32 = davidson_block<float>(pb, (float *)(slot + L.off_V), (float *)(slot + L.off_W),
+                                                     L.vec / 4, x32, (float *)(slot + L.off_hx),
+                                                     (float *)(slot + L.off_t), smem, S, a.tol_switch, 0,
+                                                     a.max_iter, true);
+                n32 += o32.nsig;
+                // (only a converged float32 eigenvalue decides; a stalled phase goes on in float64)
+                if (sector == 1)
+                    lose = o32.status == MBE_STATUS_NONFINITE ||
+                           (o32.rnorm <= a.tol_switch && o32.lambda > lam + sector_margin(lam));
+                // widen x back to float64 in place, top down
+                for (int base = ((pb.N - 1) / (int)blockDim.x) * (int)blockDim.x; base >= 0;
+                     base -= (int)blockDim.x) {
+                    int d = base + threadIdx.x;
+                    float v = (d < pb.N) ? x32[d] : 0.0f;
+                    __syncthreads();
+                    if (d < pb.N) x64[d] = (o32.status == MBE_STATUS_NONFINITE) ? 0.0 : (double)v;
+                    __syncthreads();
+                }
+                if (o32.status == MBE_STATUS_NONFINITE) {
+                    for (int d = threadIdx.x; d < pb.N; d += blockDim.x) x64[d] = sector_guess(d, pb.Ns, sg);
+                    __syncthreads();
+                }
             }
-            PhaseOut o32 = davidson_block<float>(pb, (float *)(slot + L.off_V), (float *)(slot + L.off_W),
-                                                 L.vec / 4, x32, (float *)(slot + L.off_hx),
-                                                 (float *)(slot + L.off_t), smem, S, a.tol_switch, 0, a.max_iter,
-                                                 true);
-            n32 = o32.nsig;
-            // widen x back to float64 in place, top down
-            for (int base = ((pb.N - 1) / (int)blockDim.x) * (int)blockDim.x; base >= 0; base -= (int)blockDim.x) {
-                int d = base + threadIdx.x;
-                float v = (d < pb.N) ? x32[d] : 0.0f;
-                __syncthreads();
-                if (d < pb.N) x64[d] = (o32.status == MBE_STATUS_NONFINITE) ? 0.0 : (double)v;
-                __syncthreads();
+            if (!lose) {
+                PhaseOut o64 = davidson_block<double>(pb, (double *)(slot + L.off_V), (double *)(slot + L.off_W),
+                                                      L.vec / 8, x64, (double *)(slot + L.off_hx),
+                                                      (double *)(slot + L.off_t), smem, S, a.tol,
+                                                      mixed ? a.min_fp64 : 0, a.max_iter, false);
+                n64 += o64.nsig;
+                if (sector == 0) {
+                    lam = o64.lambda;
+                    status = o64.status;
+                } else {
+                    lose = o64.status == MBE_STATUS_NONFINITE || !(o64.lambda < lam);
+                    if (!lose) {
+                        lam = o64.lambda;
+                        status = o64.status;
+                    }
+                }
             }
-            if (o32.status == MBE_STATUS_NONFINITE) {
-                for (int d = threadIdx.x; d < pb.N; d += blockDim.x)
-                    x64[d] = (d == bi ? 1.0 : 0.0) + GUESS_NOISE * guess_noise(d);
+            if (lose && a.rdm) {
                 __syncthreads();
+                for (int d = threadIdx.x; d < pb.N; d += blockDim.x) x64[d] = x2[d];
             }
+            __syncthreads();
         }
-        PhaseOut o64 = davidson_block<double>(pb, (double *)(slot + L.off_V), (double *)(slot + L.off_W),
-                                              L.vec / 8, x64, (double *)(slot + L.off_hx),
-                                              (double *)(slot + L.off_t), smem, S, a.tol,
-                                              mixed ? a.min_fp64 : 0, a.max_iter, false);
         if (threadIdx.x == 0) {
-            double e = o64.status == MBE_STATUS_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL)
-                                                         : o64.lambda - ephi - a.e_ref_corr;
-            store_result(a, t, e, o64.status, o64.nsig, n32);
+            double e = status == MBE_STATUS_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL)
+                                                      : lam - ephi - a.e_ref_corr;
+            store_result(a, t, e, status, n64, n32);
         }
         __syncthreads();
         if (a.rdm) {
@@ -1570,7 +1760,7 @@ struct Bucket {
 template <int DPL>
 static int launch_warp(mbe_ctx *ctx, const BatchArgs &a, int b, const Bucket &bk)
 {
-    WarpLayout L = warp_layout(a.n, bk.max_ns, bk.max_r, bk.max_n);
+    WarpLayout L = warp_layout(a.n, bk.max_ns, bk.max_r, bk.max_n, a.rdm != 0);
     size_t smem = (size_t)L.bytes * WARPS_PER_BLOCK;
     MBE_CHECK(smem <= ctx->smem_optin, MBE_EUNSUPPORTED, "casci_batch: warp solver needs %zu B shared memory",
               smem);
@@ -2269,7 +2459,8 @@ __global__ void __launch_bounds__(AB_MAX_THREADS) k_large_ab32(LargeCas L, int P
     const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     float *A = (float *)smem;                 // [R][Pp]
     float *B = A + (size_t)R * Pp;            // [R][AB_TJ]
-    float *srow = B + (size_t)R * AB_TJ;      // [Ns]
+    int *INV = (int *)(B + (size_t)R * AB_TJ);  // [Pp][AB_TJ], this tile's slice of inv
+    float *srow = (float *)(INV + (size_t)Pp * AB_TJ);  // [Ns]
     int *Jx = (int *)(srow + Ns);             // [R]
     const int p0 = 8 * w, j0 = 4 * lane;
     const int nB = R * AB_TJ;
@@ -2297,6 +2488,16 @@ __global__ void __launch_bounds__(AB_MAX_THREADS) k_large_ab32(LargeCas L, int P
                 if (i < nB) B[i] = pf[k];
             }
             __syncthreads();
+            // this thread's slice of inv for the tile, copied asynchronously while it multiplies
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int p = p0 + i;
+                if (p < P) {
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(INV + p * AB_TJ + j0);
+                    const int32_t *src = inv + (size_t)p * Nsp + Jb0 + j0;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+                }
+            }
             const int nxt = Jb0 + AB_TJ;
             if (nxt < Ns) {
 #pragma unroll
@@ -2311,6 +2512,7 @@ __global__ void __launch_bounds__(AB_MAX_THREADS) k_large_ab32(LargeCas L, int P
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll 2
             for (int x = 0; x < R; ++x) {
                 const float4 a0 = *(const float4 *)(A + (size_t)x * Pp + p0);
                 const float4 a1 = *(const float4 *)(A + (size_t)x * Pp + p0 + 4);
@@ -2322,11 +2524,12 @@ __global__ void __launch_bounds__(AB_MAX_THREADS) k_large_ab32(LargeCas L, int P
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
             }
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int p = p0 + i;
                 if (p < P) {
-                    const int4 e4 = *(const int4 *)(inv + (size_t)p * Nsp + Jb0 + j0);
+                    const int4 e4 = *(const int4 *)(INV + p * AB_TJ + j0);
                     const int ev[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
@@ -2562,21 +2765,23 @@ __global__ void k_copy2(const double *a, const double *b, int64_t N, double *ca,
 }
 
 // start vector: lowest diagonal element (index given) + fixed admixture
-__global__ void k_large_guess(const int64_t *best, int64_t N, double *x)
+__global__ void k_large_guess(const int64_t *best, int Ns, int sgn, int64_t N, double *x)
 {
-    const int64_t bi = best[0];
+    const SectorGuess sg{(int)best[0], sgn};
     for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < N; d += (int64_t)gridDim.x * blockDim.x)
-        x[d] = (d == bi ? 1.0 : 0.0) + GUESS_NOISE * guess_noise((int)(d & 0x7fffffff));
+        x[d] = sector_guess((int)d, Ns, sg);
 }
 
-// index of the smallest diagonal element (ties -> lowest index), one block
-__global__ void k_argmin(const double *diag, int64_t N, int64_t *out)
+// index of the smallest diagonal element (ties -> lowest index), optionally
+// among the determinants with Ia != Ib only; one block
+__global__ void k_argmin(const double *diag, int64_t N, int Ns, int open_only, int64_t *out)
 {
     __shared__ double bv[32];
     __shared__ int64_t bix[32];
     double best = 1e300;
     int64_t bi = INT64_MAX;
     for (int64_t d = threadIdx.x; d < N; d += blockDim.x) {
+        if (open_only && d / Ns == d % Ns) continue;
         double v = diag[d];
         if (v < best || (v == best && d < bi)) {
             best = v;
@@ -2760,7 +2965,8 @@ static int large_setup(mbe_ctx *ctx, int norb, const double *h1, const double *e
         MBE_CHECK(plan->ab32_threads <= AB_MAX_THREADS, MBE_EUNSUPPORTED, "large CASCI: %d pairs", P);
         MBE_CHECK((int64_t)R * AB_TJ <= (int64_t)AB_PF * plan->ab32_threads, MBE_EUNSUPPORTED,
                   "large CASCI: %d list entries exceed the float32 sigma's prefetch", R);
-        plan->smem_ab32 = (size_t)R * Pp * 4 + (size_t)R * AB_TJ * 4 + (size_t)L.Ns * 4 + (size_t)R * 4;
+        plan->smem_ab32 = (size_t)R * Pp * 4 + (size_t)R * AB_TJ * 4 + (size_t)Pp * AB_TJ * 4 + (size_t)L.Ns * 4 +
+                          (size_t)R * 4;
         MBE_CHECK(plan->smem_ab32 <= ctx->smem_optin, MBE_EUNSUPPORTED,
                   "large CASCI: float32 sigma needs %zu B shared memory", plan->smem_ab32);
         MBE_CU(cudaFuncSetAttribute(k_large_ab32, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2874,7 +3080,7 @@ __global__ void k_lincomb2(const double *V, const double *W, size_t ld, int m, c
 }
 
 struct LargeDav {
-    double *V, *W, *x, *hx, *t, *x2, *hx2, *partial, *dots, *Gd, *ys, *y2s, *misc;
+    double *V, *W, *x, *hx, *t, *x2, *hx2, *xs, *partial, *dots, *Gd, *ys, *y2s, *misc;
     float *c32;
     int64_t *best;
     size_t ld;
@@ -3028,7 +3234,7 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
     D.ld = vec / 8;
     D.nblk = ctx->sm_count * 4;
     const bool mixed = o.precision == MBE_PREC_MIXED;
-    size_t bytes = large_bytes(norb, n_cas, k0, false, mixed) + vec * (2 * MLARGE + 5) + align256((size_t)N * 4) +
+    size_t bytes = large_bytes(norb, n_cas, k0, false, mixed) + vec * (2 * MLARGE + 6) + align256((size_t)N * 4) +
                    align256((size_t)D.nblk * LRED * 8) + 8 * 256 + 4096;
     void *ws = nullptr;
     int rc = workspace(ctx, bytes, &ws);
@@ -3041,6 +3247,7 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
     D.t = bump.take<double>(D.ld);
     D.x2 = bump.take<double>(D.ld);
     D.hx2 = bump.take<double>(D.ld);
+    D.xs = bump.take<double>(D.ld);
     D.c32 = bump.take<float>((size_t)N);
     D.partial = bump.take<double>((size_t)D.nblk * LRED);
     D.dots = bump.take<double>(32);
@@ -3055,22 +3262,52 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
     // The dense one-spin Hamiltonian of the set-up lives in the (not yet used) basis region.
     rc = large_setup(ctx, norb, h1, eri, occ, n_cas, cas_orbs, bump, D.V, mixed, &pl, &k, &dphi);
     if (rc) return rc;
-    k_argmin<<<1, 1024, 0, ctx->stream>>>(pl.L.diag, N, D.best);
-    k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best, N, D.x);
+    const int Ns = pl.L.Ns;
+    k_argmin<<<1, 1024, 0, ctx->stream>>>(pl.L.diag, N, Ns, 0, D.best);
+    k_argmin<<<1, 1024, 0, ctx->stream>>>(pl.L.diag, N, Ns, 1, D.best + 1);
     ctx->launches += 2;
     double lam = 0.0, rn = 0.0;
-    int n32 = 0, n64 = 0, st32 = 0, st = 0;
-    if (mixed) {
-        rc = large_phase<float>(ctx, pl, D, o.tol_switch, 0, o.max_iter, true, &lam, &rn, &n32, &st32);
-        if (rc) return rc;
-        if (st32 == MBE_STATUS_NONFINITE) {
-            k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best, N, D.x);
-            ++ctx->launches;
+    int n32 = 0, n64 = 0, st = 0;
+    // the two spin-flip sectors (see sector_guess); each runs the float32 phase
+    // (mixed mode) and the float64 phase, and the second sector's float64 phase is
+    // skipped when its converged float32 eigenvalue lies above the first's
+    for (int sector = 0; sector < 2; ++sector) {
+        if (sector == 1 && (Ns < 2 || st != MBE_STATUS_OK)) break;
+        const int sgn = sector == 0 ? 1 : -1;
+        if (sector == 1) MBE_CU(cudaMemcpyAsync(D.xs, D.x, (size_t)N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best + sector, Ns, sgn, N, D.x);
+        ++ctx->launches;
+        double l = 0.0, r = 0.0;
+        int s64 = 0, s32 = 0, ss = MBE_STATUS_OK;
+        bool lose = false;
+        if (mixed) {
+            rc = large_phase<float>(ctx, pl, D, o.tol_switch, 0, o.max_iter, true, &l, &r, &s32, &ss);
+            if (rc) return rc;
+            if (sector == 1) lose = ss == MBE_STATUS_NONFINITE || (r <= o.tol_switch && l > lam + sector_margin(lam));
+            if (ss == MBE_STATUS_NONFINITE && !lose) {
+                k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best + sector, Ns, sgn, N, D.x);
+                ++ctx->launches;
+            }
+        }
+        if (!lose) {
+            rc = large_phase<double>(ctx, pl, D, o.tol, mixed ? o.fp64_final_iters : 0, o.max_iter, false, &l, &r,
+                                     &s64, &ss);
+            if (rc) return rc;
+        }
+        n64 += s64;
+        n32 += s32;
+        if (sector == 0) {
+            lam = l;
+            rn = r;
+            st = ss;
+        } else if (!lose && ss != MBE_STATUS_NONFINITE && l < lam) {
+            lam = l;
+            rn = r;
+            st = ss;
+        } else {
+            MBE_CU(cudaMemcpyAsync(D.x, D.xs, (size_t)N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
         }
     }
-    rc = large_phase<double>(ctx, pl, D, o.tol, mixed ? o.fp64_final_iters : 0, o.max_iter, false, &lam, &rn, &n64,
-                             &st);
-    if (rc) return rc;
     double ephi = 0.0;
     MBE_CU(cudaMemcpyAsync(&ephi, pl.L.diag + dphi, 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (cvec) MBE_CU(cudaMemcpyAsync(cvec, D.x, (size_t)N * 8, cudaMemcpyDeviceToDevice, ctx->stream));

@@ -1,0 +1,104 @@
+"""Tuple spaces whose lowest state is odd under the exchange of alpha and beta
+strings (a triplet-type state with no closed-shell component).
+
+The lowest eigenvalue of the determinant space is the target (the oracle's dense
+eigensolver); a Davidson started from the closed-shell determinant alone never
+reaches such a state, so every solver also searches the odd sector. The seeded
+8-orbital system below has 13 such tuples among its 224 (orders 2-7, the
+occupied/virtual skip rule), e.g. (0,1,2,3,4,6,7), whose odd ground state lies
+3.4e-3 E_h below the lowest even state.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import adjoint, fci, mbe as omb  # noqa: E402
+from workloads import random_system  # noqa: E402
+
+ODD = (0, 1, 2, 3, 4, 6, 7)
+
+
+@pytest.fixture(scope="module")
+def eng():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1910_03527_gb300 as e
+    e.build()
+    return e
+
+
+@pytest.fixture(scope="module")
+def ctx(eng):
+    c = eng.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def system():
+    return random_system(8, 4, seed=33)
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _swap_parity(h1, eri, occ, A):
+    k = omb.n_active_electrons(occ, A)
+    _, he, ea = omb.frozen_core(h1, eri, occ, A)
+    w, v = np.linalg.eigh(fci.h_dense(he, ea, k, k))
+    ns = math.comb(len(A), k)
+    c = v[:, 0].reshape(ns, ns)
+    return float(np.vdot(c.ravel(), c.T.ravel())), w[1] - w[0]
+
+
+def test_the_odd_case_is_odd(system):
+    h1, eri, occ = system
+    par, gap = _swap_parity(h1, eri, occ, ODD)
+    assert par < -0.999 and gap > 1e-3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tuple_energies_all_orders(eng, ctx, system, prec):
+    h1, eri, occ = system
+    exp = list(range(8))
+    e_phi = omb.phi_energy(h1, eri, occ)
+    tol = 1e-9 if prec == "fp64" else 1e-8
+    for n in range(2, 8):
+        tups = omb.tuples(exp, [], occ, n, True)
+        want = np.array([omb.tuple_energy(h1, eri, occ, [], t, e_phi, 0.0) for t in tups])
+        eps, status, _ = ctx.casci_batch(dev(h1), dev(eri), dev(occ), [], 0.0, n,
+                                         dev(np.array(tups, dtype=np.int32)), eng.Opts(precision=prec))
+        assert int((status != 0).sum()) == 0
+        assert np.abs(eps.cpu().numpy() - want).max() <= tol, n
+
+
+def test_rdm_of_the_odd_ground_state(eng, ctx, system):
+    h1, eri, occ = system
+    # casci_rdm_batch accumulates d eps / d theta = dE_CAS(A) - dE_Phi
+    _, g, G = adjoint.cas_gradient(h1, eri, occ, list(ODD))
+    _, g_phi, G_phi = adjoint.cas_gradient(h1, eri, occ, [])
+    g, G = g - g_phi, G - G_phi
+    gh = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
+    ge = torch.zeros((8,) * 4, dtype=torch.float64, device="cuda")
+    status = ctx.casci_rdm_batch(dev(h1), dev(eri), dev(occ), [], 7, dev(np.array([ODD], dtype=np.int32)),
+                                 None, gh, ge, eng.Opts(tol=1e-9))
+    assert int(status.cpu()[0]) == 0
+    assert np.abs(gh.cpu().numpy() - g).max() <= 1e-7
+    assert np.abs(ge.cpu().numpy() - G).max() <= 1e-7
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_large_solver_finds_the_odd_ground_state(eng, ctx, system, prec):
+    h1, eri, occ = system
+    k = omb.n_active_electrons(occ, ODD)
+    _, he, ea = omb.frozen_core(h1, eri, occ, list(ODD))
+    res = ctx.casci_solve(dev(h1), dev(eri), dev(occ), list(ODD), eng.Opts(precision=prec, tol=1e-7))
+    assert res["status"] == 0
+    assert abs(res["lam"] - fci.lowest_eigenvalue(he, ea, k, k)) < 1e-9
