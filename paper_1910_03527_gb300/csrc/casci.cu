@@ -832,9 +832,20 @@ __device__ inline double sector_guess(int d, int Ns, SectorGuess sg)
     return v + (d < pd ? z : sg.sgn * z);
 }
 
-// The float32 eigenvalue of the second sector must lie below the first sector's
-// eigenvalue by more than this float32 rounding margin to be refined in float64.
+// The second sector is first converged to the residual SECTOR_TOL only. Its
+// Ritz value theta then lies within the residual norm rn of an eigenvalue, so
+// when theta - rn exceeds the first sector's eigenvalue by more than a float32
+// rounding margin the sector cannot hold a lower state near theta, and it is
+// not refined further.
+constexpr double SECTOR_TOL = 1e-3;
 __host__ __device__ inline double sector_margin(double lam) { return 1e-5 * (1.0 + fabs(lam)); }
+__host__ __device__ inline bool sector_loses(double theta, double rn, double lam, double tol_conv)
+{
+    const double m = sector_margin(lam);
+    // near an eigenvalue: theta - rn bounds it from below; converged (rn <= tol_conv):
+    // theta itself is within rn^2 / gap of the sector's eigenvalue
+    return (rn <= SECTOR_TOL && theta - rn > lam + m) || (rn <= tol_conv && theta > lam + m);
+}
 
 __device__ inline void store_result(const BatchArgs &a, int64_t t, double eps, int status, int n64, int n32)
 {
@@ -966,15 +977,24 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
                 float x32[DPL];
 #pragma unroll
                 for (int j = 0; j < DPL; ++j) x32[j] = (float)x64[j];
-                PhaseOut o32 = davidson_warp<float, DPL>(pb, x32, a.tol_switch, 0, a.max_iter, true);
-                n32 += o32.nsig;
-                // (only a converged float32 eigenvalue decides; a stalled phase goes on in float64)
-                if (sector == 1)
-                    lose = o32.status == MBE_STATUS_NONFINITE ||
-                           (o32.rnorm <= a.tol_switch && o32.lambda > lam + sector_margin(lam));
-                if (o32.status != MBE_STATUS_NONFINITE && !lose)
+                // the second sector: a pass to SECTOR_TOL, then one to tol_switch if undecided
+                bool finite = true;
+                for (int pass = 0; pass < 1 + sector; ++pass) {
+                    const double tl = (sector == 0 || pass == 1) ? a.tol_switch : SECTOR_TOL;
+                    PhaseOut o32 = davidson_warp<float, DPL>(pb, x32, tl, 0, a.max_iter, true);
+                    n32 += o32.nsig;
+                    finite = o32.status != MBE_STATUS_NONFINITE;
+                    if (sector == 1)
+                        lose = !finite || sector_loses(o32.lambda, o32.rnorm, lam, a.tol_switch);
+                    if (lose || !finite) break;
+                }
+                if (finite && !lose)
 #pragma unroll
                     for (int j = 0; j < DPL; ++j) x64[j] = (double)x32[j];
+            } else if (sector == 1) {
+                PhaseOut o1 = davidson_warp<double, DPL>(pb, x64, SECTOR_TOL, 0, a.max_iter, true);
+                n64 += o1.nsig;
+                lose = o1.status == MBE_STATUS_NONFINITE || sector_loses(o1.lambda, o1.rnorm, lam, 0.0);
             }
             if (!lose) {
                 PhaseOut o64 = davidson_warp<double, DPL>(pb, x64, a.tol, mixed ? a.min_fp64 : 0, a.max_iter, false);
@@ -1594,15 +1614,19 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
                     if (d < pb.N) x32[d] = (float)v;
                     __syncthreads();
                 }
-                PhaseOut o32 = davidson_block<float>(pb, (float *)(slot + L.off_V), (float *)(slot + L.off_W),
-                                                     L.vec / 4, x32, (float *)(slot + L.off_hx),
-                                                     (float *)(slot + L.off_t), smem, S, a.tol_switch, 0,
-                                                     a.max_iter, true);
-                n32 += o32.nsig;
-                // (only a converged float32 eigenvalue decides; a stalled phase goes on in float64)
-                if (sector == 1)
-                    lose = o32.status == MBE_STATUS_NONFINITE ||
-                           (o32.rnorm <= a.tol_switch && o32.lambda > lam + sector_margin(lam));
+                // the second sector: a pass to SECTOR_TOL, then one to tol_switch if undecided
+                PhaseOut o32;
+                for (int pass = 0; pass < 1 + sector; ++pass) {
+                    const double tl = (sector == 0 || pass == 1) ? a.tol_switch : SECTOR_TOL;
+                    o32 = davidson_block<float>(pb, (float *)(slot + L.off_V), (float *)(slot + L.off_W), L.vec / 4,
+                                                x32, (float *)(slot + L.off_hx), (float *)(slot + L.off_t), smem, S,
+                                                tl, 0, a.max_iter, true);
+                    n32 += o32.nsig;
+                    if (sector == 1)
+                        lose = o32.status == MBE_STATUS_NONFINITE ||
+                               sector_loses(o32.lambda, o32.rnorm, lam, a.tol_switch);
+                    if (lose || o32.status == MBE_STATUS_NONFINITE) break;
+                }
                 // widen x back to float64 in place, top down
                 for (int base = ((pb.N - 1) / (int)blockDim.x) * (int)blockDim.x; base >= 0;
                      base -= (int)blockDim.x) {
@@ -1616,6 +1640,13 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
                     for (int d = threadIdx.x; d < pb.N; d += blockDim.x) x64[d] = sector_guess(d, pb.Ns, sg);
                     __syncthreads();
                 }
+            } else if (sector == 1) {
+                PhaseOut o1 = davidson_block<double>(pb, (double *)(slot + L.off_V), (double *)(slot + L.off_W),
+                                                     L.vec / 8, x64, (double *)(slot + L.off_hx),
+                                                     (double *)(slot + L.off_t), smem, S, SECTOR_TOL, 0,
+                                                     a.max_iter, true);
+                n64 += o1.nsig;
+                lose = o1.status == MBE_STATUS_NONFINITE || sector_loses(o1.lambda, o1.rnorm, lam, 0.0);
             }
             if (!lose) {
                 PhaseOut o64 = davidson_block<double>(pb, (double *)(slot + L.off_V), (double *)(slot + L.off_W),
@@ -3269,8 +3300,8 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
     double lam = 0.0, rn = 0.0;
     int n32 = 0, n64 = 0, st = 0;
     // the two spin-flip sectors (see sector_guess); each runs the float32 phase
-    // (mixed mode) and the float64 phase, and the second sector's float64 phase is
-    // skipped when its converged float32 eigenvalue lies above the first's
+    // (mixed mode) and the float64 phase; the second sector first runs to the
+    // residual SECTOR_TOL only and stops there when sector_loses
     for (int sector = 0; sector < 2; ++sector) {
         if (sector == 1 && (Ns < 2 || st != MBE_STATUS_OK)) break;
         const int sgn = sector == 0 ? 1 : -1;
@@ -3281,18 +3312,29 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
         int s64 = 0, s32 = 0, ss = MBE_STATUS_OK;
         bool lose = false;
         if (mixed) {
-            rc = large_phase<float>(ctx, pl, D, o.tol_switch, 0, o.max_iter, true, &l, &r, &s32, &ss);
+            rc = large_phase<float>(ctx, pl, D, sector == 0 ? o.tol_switch : SECTOR_TOL, 0, o.max_iter, true, &l, &r,
+                                    &s32, &ss);
             if (rc) return rc;
-            if (sector == 1) lose = ss == MBE_STATUS_NONFINITE || (r <= o.tol_switch && l > lam + sector_margin(lam));
+            if (sector == 1) lose = ss == MBE_STATUS_NONFINITE || sector_loses(l, r, lam, o.tol_switch);
             if (ss == MBE_STATUS_NONFINITE && !lose) {
                 k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best + sector, Ns, sgn, N, D.x);
                 ++ctx->launches;
             }
         }
-        if (!lose) {
-            rc = large_phase<double>(ctx, pl, D, o.tol, mixed ? o.fp64_final_iters : 0, o.max_iter, false, &l, &r,
-                                     &s64, &ss);
+        if (sector == 1 && !lose) {
+            // (mixed: the float32 pass stalled short of SECTOR_TOL) a float64 pass decides
+            int n = 0;
+            rc = large_phase<double>(ctx, pl, D, SECTOR_TOL, 0, o.max_iter, true, &l, &r, &n, &ss);
             if (rc) return rc;
+            s64 += n;
+            lose = ss == MBE_STATUS_NONFINITE || sector_loses(l, r, lam, 0.0);
+        }
+        if (!lose) {
+            int n = 0;
+            rc = large_phase<double>(ctx, pl, D, o.tol, mixed ? o.fp64_final_iters : 0, o.max_iter, false, &l, &r, &n,
+                                     &ss);
+            if (rc) return rc;
+            s64 += n;
         }
         n64 += s64;
         n32 += s32;
