@@ -68,6 +68,12 @@ struct BatchArgs {
     int32_t *iters;
     char *scratch;
     size_t slot_bytes;
+    // mixed mode of the warp solver split in two launches: the float32 phase leaves
+    // each tuple's start vectors (xs, float [2 * WARP_MAX_NDET] per tuple) and its
+    // state (pstate: [flag, float32 sigma count] per tuple) for the float64 phase
+    unsigned long long *counters2;
+    float *xs;
+    int32_t *pstate;
     // adjoint (casci_rdm_batch): 0 = energies only, 1 = + 1-RDM, 2 = + 1- and 2-RDM
     int rdm;
     const double *weights;
@@ -854,7 +860,17 @@ __device__ inline void store_result(const BatchArgs &a, int64_t t, double eps, i
     if (a.iters) a.iters[t] = (n64 << 16) | (n32 & 0xffff);
 }
 
-template <int DPL>
+// Warp-solver modes: WM_ALL runs both precisions in one kernel (float64 mode, and
+// the adjoint); in mixed mode WM_F32 runs the float32 phases of both spin-flip
+// sectors and decides the second, and WM_F64 finishes in float64. Split, each
+// kernel holds one precision's Davidson, which keeps the code executed on an SM
+// within the instruction cache.
+enum { WM_ALL = 0, WM_F32 = 1, WM_F64 = 2 };
+// pstate flags: the second sector lost (0), needs float64 (1); the float32 phase
+// of the first sector was not finite: redo everything in float64 (3)
+enum { PS_ONE = 0, PS_TWO = 1, PS_REDO = 3 };
+
+template <int DPL, int MODE>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
     k_casci_warp(BatchArgs a, int bucket, WarpLayout L)
 {
@@ -867,7 +883,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
     int *A = (int *)(ws + L.off_A);
     for (;;) {
         unsigned long long pos = 0;
-        if (lane == 0) pos = atomicAdd(&a.counters[bucket], 1ULL);
+        if (lane == 0) pos = atomicAdd(&(MODE == WM_F64 ? a.counters2 : a.counters)[bucket], 1ULL);
         pos = __shfl_sync(FULL, pos, 0);
         if ((int64_t)pos >= cnt) break;
         const int64_t t = a.perm[begin + (int64_t)pos];
@@ -915,7 +931,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
         int iphi = string_rank(mphi);
         double ephi = pb.diag[iphi * pb.Ns + iphi];
         if (pb.N == 1) {
-            if (lane == 0) store_result(a, t, pb.diag[0] - ephi - a.e_ref_corr, MBE_STATUS_OK, 0, 0);
+            if (MODE != WM_F32 && lane == 0) store_result(a, t, pb.diag[0] - ephi - a.e_ref_corr, MBE_STATUS_OK, 0, 0);
             __syncwarp();
             continue;
         }
@@ -950,96 +966,156 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
                 bj = oi;
             }
         }
-        double x64[DPL];
-        double *x2 = (double *)(ws + L.off_x2);
-        double lam = 0.0;
-        int status = MBE_STATUS_OK, n64 = 0, n32 = 0;
-        for (int sector = 0; sector < 2; ++sector) {
-            if (sector == 1 && (pb.Ns < 2 || status != MBE_STATUS_OK)) break;
-            const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
-            if (sector == 1 && a.rdm) {
+        float *xs_t = a.xs + (size_t)t * 2 * WARP_MAX_NDET;
+        if constexpr (MODE == WM_F32) {
+            // float32 phases: the first sector to tol_switch; the second one to
+            // SECTOR_TOL, then tol_switch, decided against the first's float32
+            // eigenvalue (whose rounding the sector margin covers)
+            int n32 = 0, flag = PS_ONE;
+            double lam32 = 0.0;
+            for (int sector = 0; sector < 2; ++sector) {
+                if (sector == 1 && pb.Ns < 2) break;
+                const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
+                pb.sector = sg.sgn;
+                float x32[DPL];
 #pragma unroll
                 for (int j = 0; j < DPL; ++j) {
                     const int d = lane + 32 * j;
-                    if (d < pb.N) x2[d] = x64[j];
+                    x32[j] = (d < pb.N) ? (float)sector_guess(d, pb.Ns, sg) : 0.f;
                 }
-            }
-            pb.sector = sg.sgn;
-#pragma unroll
-            for (int j = 0; j < DPL; ++j) {
-                const int d = lane + 32 * j;
-                x64[j] = (d < pb.N) ? sector_guess(d, pb.Ns, sg) : 0.0;
-            }
-            // the second sector is refined in float64 only if its float32
-            // eigenvalue may lie below the first sector's
-            bool lose = false;
-            if (mixed) {
-                float x32[DPL];
-#pragma unroll
-                for (int j = 0; j < DPL; ++j) x32[j] = (float)x64[j];
-                // the second sector: a pass to SECTOR_TOL, then one to tol_switch if undecided
-                bool finite = true;
+                bool finite = true, lose = false;
                 for (int pass = 0; pass < 1 + sector; ++pass) {
                     const double tl = (sector == 0 || pass == 1) ? a.tol_switch : SECTOR_TOL;
                     PhaseOut o32 = davidson_warp<float, DPL>(pb, x32, tl, 0, a.max_iter, true);
                     n32 += o32.nsig;
                     finite = o32.status != MBE_STATUS_NONFINITE;
-                    if (sector == 1)
-                        lose = !finite || sector_loses(o32.lambda, o32.rnorm, lam, a.tol_switch);
+                    if (sector == 0) lam32 = o32.lambda;
+                    if (sector == 1) lose = !finite || sector_loses(o32.lambda, o32.rnorm, lam32, a.tol_switch);
                     if (lose || !finite) break;
                 }
-                if (finite && !lose)
+                if (sector == 0 && !finite) {
+                    flag = PS_REDO;
+                    break;
+                }
+                if (sector == 1) flag = lose ? PS_ONE : PS_TWO;
+                if (sector == 0 || !lose) {
 #pragma unroll
-                    for (int j = 0; j < DPL; ++j) x64[j] = (double)x32[j];
-            } else if (sector == 1) {
-                PhaseOut o1 = davidson_warp<double, DPL>(pb, x64, SECTOR_TOL, 0, a.max_iter, true);
-                n64 += o1.nsig;
-                lose = o1.status == MBE_STATUS_NONFINITE || sector_loses(o1.lambda, o1.rnorm, lam, 0.0);
-            }
-            if (!lose) {
-                PhaseOut o64 = davidson_warp<double, DPL>(pb, x64, a.tol, mixed ? a.min_fp64 : 0, a.max_iter, false);
-                n64 += o64.nsig;
-                if (sector == 0) {
-                    lam = o64.lambda;
-                    status = o64.status;
-                } else {
-                    lose = o64.status == MBE_STATUS_NONFINITE || !(o64.lambda < lam);
-                    if (!lose) {
-                        lam = o64.lambda;
-                        status = o64.status;
+                    for (int j = 0; j < DPL; ++j) {
+                        const int d = lane + 32 * j;
+                        if (d < pb.N) xs_t[sector * pb.N + d] = x32[j];
                     }
                 }
             }
-            if (lose && a.rdm) {
-                __syncwarp();
-#pragma unroll
+            if (lane == 0) {
+                a.pstate[2 * t] = flag;
+                a.pstate[2 * t + 1] = n32;
+            }
+            __syncwarp();
+            continue;
+        } else {
+            double x64[DPL];
+            double *x2 = (double *)(ws + L.off_x2);
+            double lam = 0.0;
+            int status = MBE_STATUS_OK, n64 = 0, n32 = 0;
+            int flag = PS_REDO;
+            if constexpr (MODE == WM_F64) {
+                flag = a.pstate[2 * t];
+                n32 = a.pstate[2 * t + 1];
+            }
+            for (int sector = 0; sector < 2; ++sector) {
+                if (sector == 1 && (pb.Ns < 2 || status != MBE_STATUS_OK)) break;
+                if (MODE == WM_F64 && sector == 1 && flag == PS_ONE) break;
+                const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
+                if (sector == 1 && a.rdm) {
+    #pragma unroll
+                    for (int j = 0; j < DPL; ++j) {
+                        const int d = lane + 32 * j;
+                        if (d < pb.N) x2[d] = x64[j];
+                    }
+                }
+                pb.sector = sg.sgn;
+                const bool from_xs = MODE == WM_F64 && flag != PS_REDO;
+    #pragma unroll
                 for (int j = 0; j < DPL; ++j) {
                     const int d = lane + 32 * j;
-                    x64[j] = (d < pb.N) ? x2[d] : 0.0;
+                    x64[j] = (d < pb.N) ? (from_xs ? (double)xs_t[sector * pb.N + d] : sector_guess(d, pb.Ns, sg)) : 0.0;
                 }
+                // the second sector is refined in float64 only if its float32
+                // eigenvalue may lie below the first sector's
+                bool lose = false;
+                if constexpr (MODE == WM_ALL) if (mixed) {
+                    float x32[DPL];
+    #pragma unroll
+                    for (int j = 0; j < DPL; ++j) x32[j] = (float)x64[j];
+                    // the second sector: a pass to SECTOR_TOL, then one to tol_switch if undecided
+                    bool finite = true;
+                    for (int pass = 0; pass < 1 + sector; ++pass) {
+                        const double tl = (sector == 0 || pass == 1) ? a.tol_switch : SECTOR_TOL;
+                        PhaseOut o32 = davidson_warp<float, DPL>(pb, x32, tl, 0, a.max_iter, true);
+                        n32 += o32.nsig;
+                        finite = o32.status != MBE_STATUS_NONFINITE;
+                        if (sector == 1)
+                            lose = !finite || sector_loses(o32.lambda, o32.rnorm, lam, a.tol_switch);
+                        if (lose || !finite) break;
+                    }
+                    if (finite && !lose)
+    #pragma unroll
+                        for (int j = 0; j < DPL; ++j) x64[j] = (double)x32[j];
+                }
+                // float64: in float64 mode the second sector's first pass (to SECTOR_TOL)
+                // decides; one call site keeps the kernel within the instruction cache
+                const bool pure64 = !mixed || (MODE == WM_F64 && flag == PS_REDO);
+                for (int pass = (sector == 1 && pure64) ? 0 : 1; pass < 2 && !lose; ++pass) {
+                    const bool first = pass == 0;
+                    PhaseOut o64 = davidson_warp<double, DPL>(pb, x64, first ? SECTOR_TOL : a.tol,
+                                                              (first || pure64) ? 0 : a.min_fp64, a.max_iter, first);
+                    n64 += o64.nsig;
+                    if (first) {
+                        lose = o64.status == MBE_STATUS_NONFINITE || sector_loses(o64.lambda, o64.rnorm, lam, 0.0);
+                        continue;
+                    }
+                    if (sector == 0) {
+                        lam = o64.lambda;
+                        status = o64.status;
+                    } else {
+                        lose = o64.status == MBE_STATUS_NONFINITE || !(o64.lambda < lam);
+                        if (!lose) {
+                            lam = o64.lambda;
+                            status = o64.status;
+                        }
+                    }
+                }
+                if (lose && a.rdm) {
+                    __syncwarp();
+    #pragma unroll
+                    for (int j = 0; j < DPL; ++j) {
+                        const int d = lane + 32 * j;
+                        x64[j] = (d < pb.N) ? x2[d] : 0.0;
+                    }
+                }
+                __syncwarp();
+            }
+            if (lane == 0) {
+                double e = status == MBE_STATUS_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL)
+                                                          : lam - ephi - a.e_ref_corr;
+                store_result(a, t, e, status, n64, n32);
             }
             __syncwarp();
-        }
-        if (lane == 0) {
-            double e = status == MBE_STATUS_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL)
-                                                      : lam - ephi - a.e_ref_corr;
-            store_result(a, t, e, status, n64, n32);
-        }
-        __syncwarp();
-        if (a.rdm) {
-            double *cv = (double *)pb.c;
-            double *g1 = (double *)(ws + L.off_g1);
-#pragma unroll
-            for (int j = 0; j < DPL; ++j) {
-                int d = lane + 32 * j;
-                if (d < pb.N) cv[d] = x64[j];
+            if (a.rdm) {
+                double *cv = (double *)pb.c;
+                double *g1 = (double *)(ws + L.off_g1);
+    #pragma unroll
+                for (int j = 0; j < DPL; ++j) {
+                    int d = lane + 32 * j;
+                    if (d < pb.N) cv[d] = x64[j];
+                }
+                for (int e = lane; e < n * n; e += 32) g1[e] = 0.0;
+                __syncwarp();
+                rdm_accumulate<WarpGroup>(pb, cv, g1, nullptr);
+                __syncwarp();
+                rdm_flush<WarpGroup>(a, pb, g1, nullptr, a.weights ? a.weights[t] : 1.0);
+                __syncwarp();
             }
-            for (int e = lane; e < n * n; e += 32) g1[e] = 0.0;
-            __syncwarp();
-            rdm_accumulate<WarpGroup>(pb, cv, g1, nullptr);
-            __syncwarp();
-            rdm_flush<WarpGroup>(a, pb, g1, nullptr, a.weights ? a.weights[t] : 1.0);
-            __syncwarp();
         }
     }
 }
@@ -1788,6 +1864,22 @@ struct Bucket {
     int max_ns, max_r, max_n;
 };
 
+template <int DPL, int MODE>
+static int launch_warp_mode(mbe_ctx *ctx, const BatchArgs &a, int b, const WarpLayout &L, size_t smem)
+{
+    MBE_CU(cudaFuncSetAttribute(k_casci_warp<DPL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_casci_warp<DPL, MODE>, WARPS_PER_BLOCK * 32,
+                                                         smem));
+    if (per_sm < 1) per_sm = 1;
+    k_casci_warp<DPL, MODE><<<ctx->sm_count * per_sm, WARPS_PER_BLOCK * 32, smem, ctx->stream>>>(a, b, L);
+    MBE_CU(cudaGetLastError());
+    ++ctx->launches;
+    return MBE_OK;
+}
+
+// One warp-solver bucket: in mixed mode (energies only) a float32 launch and a
+// float64 launch, timed as one.
 template <int DPL>
 static int launch_warp(mbe_ctx *ctx, const BatchArgs &a, int b, const Bucket &bk)
 {
@@ -1795,15 +1887,14 @@ static int launch_warp(mbe_ctx *ctx, const BatchArgs &a, int b, const Bucket &bk
     size_t smem = (size_t)L.bytes * WARPS_PER_BLOCK;
     MBE_CHECK(smem <= ctx->smem_optin, MBE_EUNSUPPORTED, "casci_batch: warp solver needs %zu B shared memory",
               smem);
-    MBE_CU(cudaFuncSetAttribute(k_casci_warp<DPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_casci_warp<DPL>, WARPS_PER_BLOCK * 32, smem));
-    if (per_sm < 1) per_sm = 1;
-    int grid = ctx->sm_count * per_sm;
     TimedLaunch tl(ctx, a.order, 0, DPL);
-    k_casci_warp<DPL><<<grid, WARPS_PER_BLOCK * 32, smem, ctx->stream>>>(a, b, L);
-    MBE_CU(cudaGetLastError());
-    ++ctx->launches;
+    int rc;
+    if (a.xs != nullptr) {
+        if ((rc = launch_warp_mode<DPL, WM_F32>(ctx, a, b, L, smem))) return rc;
+        if ((rc = launch_warp_mode<DPL, WM_F64>(ctx, a, b, L, smem))) return rc;
+    } else {
+        if ((rc = launch_warp_mode<DPL, WM_ALL>(ctx, a, b, L, smem))) return rc;
+    }
     return tl.done();
 }
 
@@ -1934,9 +2025,14 @@ static int run_casci(mbe_ctx *ctx, int norb, const double *h1, const double *eri
     }
 
     const bool own_out = (eps_out == nullptr || status_out == nullptr);
+    // mixed mode without density matrices splits the warp solver in two launches
+    bool any_warp = false;
+    for (const Bucket &bk : buckets) any_warp = any_warp || bk.warp;
+    const bool split = any_warp && a.precision == MBE_PREC_MIXED && rdm == 0;
     size_t bytes = align256((size_t)norb * norb * 8) + align256((size_t)n_tuples * 4) * 2 +
-                   4 * align256((MAX_BUCKETS + 1) * 8) + (size_t)block_grid_n * slot_bytes +
+                   5 * align256((MAX_BUCKETS + 1) * 8) + (size_t)block_grid_n * slot_bytes +
                    (own_out ? align256((size_t)n_tuples * 8) + align256((size_t)n_tuples * 4) : 0) + 1024;
+    if (split) bytes += align256((size_t)n_tuples * 2 * WARP_MAX_NDET * 4) + align256((size_t)n_tuples * 8);
     void *ws = nullptr;
     int rc = workspace(ctx, bytes, &ws);
     if (rc) return rc;
@@ -1947,9 +2043,16 @@ static int run_casci(mbe_ctx *ctx, int norb, const double *h1, const double *eri
     int64_t *counts = bump.take<int64_t>(MAX_BUCKETS + 1);
     unsigned long long *cursor = bump.take<unsigned long long>(MAX_BUCKETS + 1);
     unsigned long long *counters = bump.take<unsigned long long>(MAX_BUCKETS + 1);
+    unsigned long long *counters2 = bump.take<unsigned long long>(MAX_BUCKETS + 1);
     int64_t *bucket_off = bump.take<int64_t>(MAX_BUCKETS + 1);
     char *scratch = nullptr;
     if (block_grid_n > 0) scratch = bump.take<char>((size_t)block_grid_n * slot_bytes);
+    a.xs = nullptr;
+    a.pstate = nullptr;
+    if (split) {
+        a.xs = bump.take<float>((size_t)n_tuples * 2 * WARP_MAX_NDET);
+        a.pstate = bump.take<int32_t>((size_t)n_tuples * 2);
+    }
     if (own_out) {
         a.eps = bump.take<double>((size_t)n_tuples);
         a.status = status_out ? status_out : bump.take<int32_t>((size_t)n_tuples);
@@ -1964,10 +2067,11 @@ static int run_casci(mbe_ctx *ctx, int norb, const double *h1, const double *eri
     a.perm = perm;
     a.bucket_off = bucket_off;
     a.counters = counters;
+    a.counters2 = counters2;
     a.scratch = scratch;
     a.slot_bytes = slot_bytes;
 
-    MBE_CU(cudaMemsetAsync(counts, 0, 3 * align256((MAX_BUCKETS + 1) * 8), ctx->stream));
+    MBE_CU(cudaMemsetAsync(counts, 0, 4 * align256((MAX_BUCKETS + 1) * 8), ctx->stream));
     k_core_fock<<<(norb * norb + 127) / 128, 128, 0, ctx->stream>>>(norb, h1, eri, occ, F);
     unsigned g = (unsigned)((n_tuples + 255) / 256);
     k_classify<<<g, 256, 0, ctx->stream>>>(a, cl, key, counts);
@@ -2278,6 +2382,7 @@ extern "C" int casci_sigma_noalloc(int device, void *cuda_stream, int norb, cons
 namespace mbe {
 
 constexpr int MLARGE = 12;      // Davidson basis of the large solver (<= MMAX)
+constexpr int LARGE_STALL = 20; // float32 iterations without a 10% residual drop that end a phase
 constexpr int LRED = MLARGE + 2;  // values per grid reduction
 constexpr int LARGE_THREADS = 256;
 constexpr int SIGMA_THREADS = 512;
@@ -3186,7 +3291,7 @@ static int large_phase(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, dou
             if (rn < 0.9 * best) {
                 best = rn;
                 stall = 0;
-            } else if (++stall >= 3) {
+            } else if (++stall >= LARGE_STALL) {
                 break;
             }
         }
@@ -3300,8 +3405,8 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
     double lam = 0.0, rn = 0.0;
     int n32 = 0, n64 = 0, st = 0;
     // the two spin-flip sectors (see sector_guess); each runs the float32 phase
-    // (mixed mode) and the float64 phase; the second sector first runs to the
-    // residual SECTOR_TOL only and stops there when sector_loses
+    // (mixed mode) and the float64 phase; the second sector first runs a float64
+    // pass to the residual SECTOR_TOL only and stops there when sector_loses
     for (int sector = 0; sector < 2; ++sector) {
         if (sector == 1 && (Ns < 2 || st != MBE_STATUS_OK)) break;
         const int sgn = sector == 0 ? 1 : -1;
@@ -3311,23 +3416,22 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
         double l = 0.0, r = 0.0;
         int s64 = 0, s32 = 0, ss = MBE_STATUS_OK;
         bool lose = false;
-        if (mixed) {
-            rc = large_phase<float>(ctx, pl, D, sector == 0 ? o.tol_switch : SECTOR_TOL, 0, o.max_iter, true, &l, &r,
-                                    &s32, &ss);
-            if (rc) return rc;
-            if (sector == 1) lose = ss == MBE_STATUS_NONFINITE || sector_loses(l, r, lam, o.tol_switch);
-            if (ss == MBE_STATUS_NONFINITE && !lose) {
-                k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best + sector, Ns, sgn, N, D.x);
-                ++ctx->launches;
-            }
-        }
-        if (sector == 1 && !lose) {
-            // (mixed: the float32 pass stalled short of SECTOR_TOL) a float64 pass decides
+        if (sector == 1) {
+            // a float64 pass from the start vector to SECTOR_TOL decides (a float32
+            // pass of this slowly converging solver stalls short of it)
             int n = 0;
             rc = large_phase<double>(ctx, pl, D, SECTOR_TOL, 0, o.max_iter, true, &l, &r, &n, &ss);
             if (rc) return rc;
             s64 += n;
             lose = ss == MBE_STATUS_NONFINITE || sector_loses(l, r, lam, 0.0);
+        }
+        if (!lose && mixed) {
+            rc = large_phase<float>(ctx, pl, D, o.tol_switch, 0, o.max_iter, true, &l, &r, &s32, &ss);
+            if (rc) return rc;
+            if (ss == MBE_STATUS_NONFINITE) {
+                k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best + sector, Ns, sgn, N, D.x);
+                ++ctx->launches;
+            }
         }
         if (!lose) {
             int n = 0;
