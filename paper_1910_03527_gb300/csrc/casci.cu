@@ -2382,7 +2382,7 @@ extern "C" int casci_sigma_noalloc(int device, void *cuda_stream, int norb, cons
 namespace mbe {
 
 constexpr int MLARGE = 12;      // Davidson basis of the large solver (<= MMAX)
-constexpr int LARGE_STALL = 20; // float32 iterations without a 10% residual drop that end a phase
+constexpr int LARGE_STALL = 20; // iterations without a 10% residual drop that end the sector-deciding pass
 constexpr int LRED = MLARGE + 2;  // values per grid reduction
 constexpr int LARGE_THREADS = 256;
 constexpr int SIGMA_THREADS = 512;
@@ -3244,7 +3244,7 @@ static int large_apply(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, con
 // vector in, Ritz vector out.
 template <typename T>
 static int large_phase(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, double tol, int min_iter,
-                       int max_iter, bool steer, double *lambda, double *rnorm, int *nsig, int *status)
+                       int max_iter, int steer, double *lambda, double *rnorm, int *nsig, int *status)
 {
     const int64_t N = pl.L.N;
     const size_t ld = D.ld;
@@ -3291,7 +3291,7 @@ static int large_phase(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, dou
             if (rn < 0.9 * best) {
                 best = rn;
                 stall = 0;
-            } else if (++stall >= LARGE_STALL) {
+            } else if (++stall >= steer) {
                 break;
             }
         }
@@ -3420,13 +3420,13 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
             // a float64 pass from the start vector to SECTOR_TOL decides (a float32
             // pass of this slowly converging solver stalls short of it)
             int n = 0;
-            rc = large_phase<double>(ctx, pl, D, SECTOR_TOL, 0, o.max_iter, true, &l, &r, &n, &ss);
+            rc = large_phase<double>(ctx, pl, D, SECTOR_TOL, 0, o.max_iter, LARGE_STALL, &l, &r, &n, &ss);
             if (rc) return rc;
             s64 += n;
             lose = ss == MBE_STATUS_NONFINITE || sector_loses(l, r, lam, 0.0);
         }
         if (!lose && mixed) {
-            rc = large_phase<float>(ctx, pl, D, o.tol_switch, 0, o.max_iter, true, &l, &r, &s32, &ss);
+            rc = large_phase<float>(ctx, pl, D, o.tol_switch, 0, o.max_iter, 3, &l, &r, &s32, &ss);
             if (rc) return rc;
             if (ss == MBE_STATUS_NONFINITE) {
                 k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best + sector, Ns, sgn, N, D.x);
@@ -3435,7 +3435,7 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
         }
         if (!lose) {
             int n = 0;
-            rc = large_phase<double>(ctx, pl, D, o.tol, mixed ? o.fp64_final_iters : 0, o.max_iter, false, &l, &r, &n,
+            rc = large_phase<double>(ctx, pl, D, o.tol, mixed ? o.fp64_final_iters : 0, o.max_iter, 0, &l, &r, &n,
                                      &ss);
             if (rc) return rc;
             s64 += n;
