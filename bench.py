@@ -565,6 +565,53 @@ def run_screened(args):
     ctx.close()
 
 
+def run_molecule(args):
+    """The synthetic 40-orbital molecule (seed 1910): (6e,6o) reference space
+    {5..10}, expansion over the other 34 orbitals, orders 1..max_order, mixed
+    precision, one pass after an order-1 warm-up; tuple CASCIs of 7-10 orbitals
+    (up to 63,504 determinants, block solver)."""
+    import torch
+
+    import paper_1910_03527_gb300 as eng
+    from workloads import workload
+
+    eng.build()
+    w = workload("molecule40")
+    dev = torch.device("cuda", 0)
+    ctx = eng.Context(0)
+    th1, teri, tocc = (torch.tensor(x, device=dev) for x in (w.h1, w.eri, w.occ))
+    occ_h = [int(v) for v in w.occ]
+    orders = list(range(1, args.molecule_max_order + 1))
+    out = {"metric": "tuple CASCI solves/s, synthetic 40-orbital molecule", "unit": UNIT,
+           "workload": "synthetic 40-orbital molecule (seed 1910), (6e,6o) reference {5..10}, "
+                       f"34 expansion orbitals, orders 1-{orders[-1]}, no skip rule", "per_precision": {}}
+    for prec in args.molecule_precisions:
+        opts = eng.Opts(precision=prec)
+        eng.run_mbe(ctx, th1, teri, tocc, w.ref, w.exp, [1], False, opts, occ_host=occ_h)
+        torch.cuda.synchronize()
+        ctx.take_timings()
+        ctx.set_timing(True)
+        t0 = time.perf_counter()
+        res = eng.run_mbe(ctx, th1, teri, tocc, w.ref, w.exp, orders, False, opts, occ_host=occ_h)
+        e_tot = float(res["e_total"].item())
+        t = time.perf_counter() - t0
+        recs = ctx.take_timings()
+        ctx.set_timing(False)
+        per_order = {}
+        for i, n in enumerate(orders):
+            ms = sum(r[3] for r in recs if r[0] == n)
+            nt = int(res["tuples"][i].shape[0])
+            it = res["iters"][i]
+            per_order[n] = {"tuples": nt, "solver_ms": ms, "solves_per_s": nt / (ms / 1e3) if ms > 0 else None,
+                            "fp64_sigma_per_tuple": float(((it >> 16) & 0xffff).double().mean().item()) if nt else 0,
+                            "fp32_sigma_per_tuple": float((it & 0xffff).double().mean().item()) if nt else 0,
+                            "non_ok": int((res["status"][i] != 0).sum().item())}
+        n_t = sum(v["tuples"] for v in per_order.values())
+        out["per_precision"][prec] = {"value": n_t / t, "seconds": t, "e_total": e_tot, "per_order": per_order}
+    print(json.dumps(out))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -586,7 +633,14 @@ def main():
                     help="screened expansion (Eq. 4) on a Hubbard ring: tuples per order and solves/s")
     ap.add_argument("--screened-workload", default="hubbard22", choices=["hubbard22", "hubbard46"])
     ap.add_argument("--screened-max-order", type=int, default=8)
+    ap.add_argument("--molecule", action="store_true",
+                    help="the synthetic 40-orbital molecule: solves/s per order (block-solver sizes)")
+    ap.add_argument("--molecule-max-order", type=int, default=3)
+    ap.add_argument("--molecule-precisions", nargs="+", default=["mixed"], choices=["mixed", "fp64"])
     args = ap.parse_args()
+    if args.molecule:
+        run_molecule(args)
+        return
     if args.large:
         run_large(args)
         return

@@ -792,7 +792,9 @@ struct WarpLayout {
 
 __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 
-__host__ __device__ inline WarpLayout warp_layout(int n, int ns, int r, int N, bool keep_vector)
+// vbytes: bytes per element of the Davidson's shared vectors c and sbuf (4 in
+// the float32-only launch of mixed mode, else 8)
+__host__ __device__ inline WarpLayout warp_layout(int n, int ns, int r, int N, bool keep_vector, int vbytes = 8)
 {
     WarpLayout L;
     int P = n * (n + 1) / 2, HSS = odd_stride(ns), RS = odd_stride(r > 0 ? r : 1);
@@ -806,8 +808,8 @@ __host__ __device__ inline WarpLayout warp_layout(int n, int ns, int r, int N, b
     L.off_Hs64 = o; o = al16(o + 8 * ns * HSS);
     L.off_Hs32 = o; o = al16(o + 4 * ns * HSS);
     L.off_diag = o; o = al16(o + 8 * N);
-    L.off_c = o; o = al16(o + 8 * N);
-    L.off_s = o; o = al16(o + 8 * N);
+    L.off_c = o; o = al16(o + vbytes * N);
+    L.off_s = o; o = al16(o + vbytes * N);
     L.off_str = o; o = al16(o + 4 * ns);
     L.off_tab = o; o = al16(o + 4 * ns * RS);
     L.off_g1 = o; o = al16(o + 8 * n * n);
@@ -1890,7 +1892,8 @@ static int launch_warp(mbe_ctx *ctx, const BatchArgs &a, int b, const Bucket &bk
     TimedLaunch tl(ctx, a.order, 0, DPL);
     int rc;
     if (a.xs != nullptr) {
-        if ((rc = launch_warp_mode<DPL, WM_F32>(ctx, a, b, L, smem))) return rc;
+        const WarpLayout L32 = warp_layout(a.n, bk.max_ns, bk.max_r, bk.max_n, false, 4);
+        if ((rc = launch_warp_mode<DPL, WM_F32>(ctx, a, b, L32, (size_t)L32.bytes * WARPS_PER_BLOCK))) return rc;
         if ((rc = launch_warp_mode<DPL, WM_F64>(ctx, a, b, L, smem))) return rc;
     } else {
         if ((rc = launch_warp_mode<DPL, WM_ALL>(ctx, a, b, L, smem))) return rc;
