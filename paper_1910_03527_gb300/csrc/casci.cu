@@ -1124,8 +1124,8 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
 
 // ------------------------------------------------------------------ block solver
 
-constexpr int MMAX = 12;  // Davidson subspace of the block solver
-constexpr int KRED = 16;  // values per block reduction (>= MMAX + 1)
+constexpr int MMAX = 20;  // Davidson subspace of the block solver
+constexpr int KRED = 24;  // values per block reduction (>= MMAX + 1)
 
 // Per-block workspace slot: the Davidson basis V, its image W = H V, the Ritz
 // vector x and H x, a spare correction vector, the diagonal and Hs.
