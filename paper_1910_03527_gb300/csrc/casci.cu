@@ -1126,6 +1126,10 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
 
 constexpr int MMAX = 20;  // Davidson subspace of the block solver
 constexpr int KRED = 24;  // values per block reduction (>= MMAX + 1)
+// float32 iterations without a 10% residual drop that end the block solver's float32
+// phase (a window of 10 moved work into float32 on the 40-orbital molecule but took
+// longer: this solver's float32 sigma is not much cheaper than its float64 one)
+constexpr int BLOCK_STALL = 3;
 
 // Per-block workspace slot: the Davidson basis V, its image W = H V, the Ritz
 // vector x and H x, a spare correction vector, the diagonal and Hs.
@@ -1440,7 +1444,7 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
             if (rn < (T)0.9 * best) {
                 best = rn;
                 stall = 0;
-            } else if (++stall >= 3) {
+            } else if (++stall >= BLOCK_STALL) {
                 break;
             }
         }
