@@ -443,11 +443,13 @@ def run_ncu_case(args):
     from workloads import workload
 
     eng.build()
-    w = workload(WORKLOAD)
+    w = workload(args.ncu_workload)
     dev = torch.device("cuda", 0)
     ctx = eng.Context(0)
     h1, eri, occ = (torch.tensor(x, device=dev) for x in (w.h1, w.eri, w.occ))
     tup = ctx.mbe_tuples(w.norb, w.occ.tolist(), w.exp, w.ref, args.ncu_order, w.skip)
+    if args.ncu_tuples:
+        tup = tup[: args.ncu_tuples].contiguous()
     opts = eng.Opts(precision=args.ncu_case)
     for _ in range(max(args.steps, 1)):
         eps, st, it = ctx.casci_batch(h1, eri, occ, w.ref, 0.0, args.ncu_order, tup, opts)
@@ -627,6 +629,8 @@ def main():
     ap.add_argument("--ncu-case", choices=["fp64", "mixed"], default=None,
                     help="run only casci_batch on one order of the workload (for ncu captures)")
     ap.add_argument("--ncu-order", type=int, default=6)
+    ap.add_argument("--ncu-workload", default=WORKLOAD, choices=["hubbard22", "molecule40"])
+    ap.add_argument("--ncu-tuples", type=int, default=0, help="--ncu-case: only the first N tuples")
     ap.add_argument("--large", action="store_true",
                     help="single large CASCI: sigma throughput at 12/14/16 orbitals and a 12-orbital solve")
     ap.add_argument("--large-sizes", type=int, nargs="+", default=[12, 14, 16])
