@@ -3432,7 +3432,9 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
             s64 += n;
             lose = ss == MBE_STATUS_NONFINITE || sector_loses(l, r, lam, 0.0);
         }
-        if (!lose && mixed) {
+        // (the second sector, when it may lie lower, goes on in float64 from its
+        // deciding pass, as in float64 mode)
+        if (!lose && mixed && sector == 0) {
             rc = large_phase<float>(ctx, pl, D, o.tol_switch, 0, o.max_iter, 3, &l, &r, &s32, &ss);
             if (rc) return rc;
             if (ss == MBE_STATUS_NONFINITE) {
@@ -3442,7 +3444,8 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
         }
         if (!lose) {
             int n = 0;
-            rc = large_phase<double>(ctx, pl, D, o.tol, mixed ? o.fp64_final_iters : 0, o.max_iter, 0, &l, &r, &n,
+            rc = large_phase<double>(ctx, pl, D, o.tol, (mixed && sector == 0) ? o.fp64_final_iters : 0, o.max_iter, 0,
+                                     &l, &r, &n,
                                      &ss);
             if (rc) return rc;
             s64 += n;
