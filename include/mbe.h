@@ -222,9 +222,8 @@ int casci_sigma(mbe_ctx *ctx, int norb, const double *h1, const double *eri, con
  * Allocation-free variant of casci_sigma.  The paper has no counterpart: it
  * serves callers that cannot allocate device memory when they call, such as a
  * host application whose memory is owned by its own pool or allocator, code
- * running under a hard real-time or stream-capture discipline in which
- * cudaMalloc would stall or be illegal, or a plug-in that must not grow device
- * memory behind its host's back.
+ * running under a hard real-time discipline in which cudaMalloc would stall,
+ * or a plug-in that must not grow device memory behind its host's back.
  *
  * The call computes the same sigma = H_A c (and the diagonal) as casci_sigma,
  * for the sector with n_el alpha and n_el beta electrons in the active space
