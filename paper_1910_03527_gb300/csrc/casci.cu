@@ -845,7 +845,7 @@ __device__ inline double sector_guess(int d, int Ns, SectorGuess sg)
 // when theta - rn exceeds the first sector's eigenvalue by more than a float32
 // rounding margin the sector cannot hold a lower state near theta, and it is
 // not refined further.
-constexpr double SECTOR_TOL = 1e-3;
+constexpr double SECTOR_TOL = 1e-2;
 __host__ __device__ inline double sector_margin(double lam) { return 1e-5 * (1.0 + fabs(lam)); }
 __host__ __device__ inline bool sector_loses(double theta, double rn, double lam, double tol_conv)
 {
