@@ -79,7 +79,7 @@ typedef struct mbe_opts {
     int fp64_final_iters; /* mixed mode: minimum float64 iterations                  */
 } mbe_opts;
 
-/* Fills *opts with the defaults: FP64, tol 1e-6, tol_switch 1e-5, max_iter 500,
+/* Fills *opts with the defaults: FP64, tol 1e-6, tol_switch 1e-5, max_iter 2000,
    fp64_final_iters 2.  Host only, synchronous. */
 void mbe_default_opts(mbe_opts *opts);
 

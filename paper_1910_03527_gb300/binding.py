@@ -135,7 +135,7 @@ class Opts:
     precision: str = "fp64"  # "fp64" or "mixed"
     tol: float = 1e-6
     tol_switch: float = 1e-5
-    max_iter: int = 500
+    max_iter: int = 2000
     fp64_final_iters: int = 2
 
     def to_c(self) -> MbeOpts:

@@ -115,7 +115,7 @@ void mbe_default_opts(mbe_opts *o)
     o->precision = MBE_PREC_FP64;
     o->tol = 1e-6;
     o->tol_switch = 1e-5;
-    o->max_iter = 500;
+    o->max_iter = 2000;
     o->fp64_final_iters = 2;
 }
 
