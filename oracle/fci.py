@@ -182,3 +182,53 @@ def lowest_eigenpair(h: np.ndarray, eri: np.ndarray, na: int, nb: int, tol: floa
 
 def lowest_eigenvalue(h, eri, na, nb, tol: float = 1e-13) -> float:
     return lowest_eigenpair(h, eri, na, nb, tol=tol)
+
+
+def even_sector_basis(n: int, ne: int):
+    """Orthonormal basis (sparse, N x M) of the determinant vectors that are even
+    under the exchange of the alpha and beta strings, c[Ia][Ib] = c[Ib][Ia]
+    (n_alpha = n_beta = ne): e_d for Ia = Ib, (e_d + e_Pd)/sqrt(2) for Ia < Ib."""
+    import scipy.sparse
+
+    ns = binom(n, ne)
+    rows, cols, vals = [], [], []
+    m = 0
+    for ia in range(ns):
+        for ib in range(ia, ns):
+            d, pd = ia * ns + ib, ib * ns + ia
+            if d == pd:
+                rows.append(d)
+                cols.append(m)
+                vals.append(1.0)
+            else:
+                rows += [d, pd]
+                cols += [m, m]
+                vals += [2.0 ** -0.5, 2.0 ** -0.5]
+            m += 1
+    return scipy.sparse.csr_matrix((vals, (rows, cols)), shape=(ns * ns, m))
+
+
+def lowest_eigenvalue_even(h: np.ndarray, eri: np.ndarray, ne: int, tol: float = 1e-13) -> float:
+    """Lowest eigenvalue of the CAS Hamiltonian restricted to the even sector of
+    the alpha-beta string exchange (the sector of the closed-shell
+    determinants; for M_S = 0 these are the states of even total spin):
+    Q^T H Q with Q from even_sector_basis, by LAPACK or ARPACK."""
+    import scipy.linalg
+    import scipy.sparse
+    import scipy.sparse.linalg
+
+    n = h.shape[0]
+    N = binom(n, ne) ** 2
+    Q = even_sector_basis(n, ne)
+    if N <= DENSE_MAX:
+        H = h_dense(h, eri, ne, ne)
+        Hq = Q.T @ (Q.T @ H.T).T
+        w = scipy.linalg.eigh(np.asarray(Hq), eigvals_only=True, subset_by_index=[0, 0])
+        return float(w[0])
+    rows, cols, vals = h_coo(h, eri, ne, ne)
+    A = scipy.sparse.csr_matrix((vals, (rows, cols)), shape=(N, N))
+    Hq = (Q.T @ A @ Q).tocsr()
+    v0 = np.cos(np.arange(Hq.shape[0]) * 0.7311) + 0.1
+    w = scipy.sparse.linalg.eigsh(Hq, k=1, which="SA", tol=tol, v0=v0, ncv=min(Hq.shape[0], 40),
+                                  return_eigenvectors=False)
+    return float(w[0])

@@ -99,13 +99,17 @@ def n_active_electrons(occ: np.ndarray, A: Sequence[int]) -> int:
     return int(sum(int(occ[p]) for p in A))
 
 
-def casci_energy(h1, eri, occ, A, tol: float = 1e-13) -> float:
-    """E_CAS(A) = E_core + lowest eigenvalue of the A-space Hamiltonian."""
+def casci_energy(h1, eri, occ, A, tol: float = 1e-13, even_only: bool = False) -> float:
+    """E_CAS(A) = E_core + lowest eigenvalue of the A-space Hamiltonian; with
+    even_only, the lowest one that is even under the alpha-beta string exchange
+    (the closed-shell determinant's sector: states of even total spin)."""
     A = sorted(A)
     e_core, h_eff, eri_a = frozen_core(h1, eri, occ, A)
     if len(A) == 0:
         return e_core
     ne = n_active_electrons(occ, A)
+    if even_only:
+        return e_core + fci.lowest_eigenvalue_even(h_eff, eri_a, ne, tol=tol)
     lam = fci.lowest_eigenvalue(h_eff, eri_a, ne, ne, tol=tol)
     return e_core + lam
 
@@ -117,10 +121,10 @@ def ref_corr_energy(h1, eri, occ, ref: Sequence[int]) -> float:
     return casci_energy(h1, eri, occ, ref) - phi_energy(h1, eri, occ)
 
 
-def tuple_energy(h1, eri, occ, ref, tup, e_phi: float, e_ref_corr: float) -> float:
+def tuple_energy(h1, eri, occ, ref, tup, e_phi: float, e_ref_corr: float, even_only: bool = False) -> float:
     """eps(Omega) = E_CAS(R u Omega) - E_Phi - E_ref,corr."""
     A = sorted(set(ref) | set(tup))
-    return casci_energy(h1, eri, occ, A) - e_phi - e_ref_corr
+    return casci_energy(h1, eri, occ, A, even_only=even_only) - e_phi - e_ref_corr
 
 
 def keep_tuple(tup: Sequence[int], ref: Sequence[int], occ: np.ndarray) -> bool:

@@ -68,3 +68,34 @@ def test_hubbard_tuple_ground_states_are_even():
             par, gap = _lowest_parity(h1, eri, occ, t)
             if gap > 1e-8:
                 assert par > 0.999, t
+
+
+def test_even_sector_eigenvalue_pins():
+    from oracle import fci as f
+    h1, eri, occ = random_system(8, 4, seed=33)
+    # the odd-ground tuple: the even-sector value is the lowest full eigenvalue
+    # whose eigenvector is even, found here by classifying all eigenvectors
+    A = [0, 1, 2, 3, 4, 6, 7]
+    k = omb.n_active_electrons(occ, A)
+    _, he, ea = omb.frozen_core(h1, eri, occ, A)
+    H = fci.h_dense(he, ea, k, k)
+    w, v = np.linalg.eigh(H)
+    ns = math.comb(len(A), k)
+    par = [float(np.vdot(v[:, i], v[:, i].reshape(ns, ns).T.ravel())) for i in range(len(w))]
+    first_even = next(w[i] for i in range(len(w)) if par[i] > 0.5)
+    assert abs(f.lowest_eigenvalue_even(he, ea, k) - first_even) < 1e-12
+    assert f.lowest_eigenvalue_even(he, ea, k) > w[0] + 1e-3
+    # the basis: orthonormal, spans exactly the even vectors (dimension Ns(Ns+1)/2)
+    for n, ne in ((4, 2), (6, 3), (5, 1)):
+        Q = f.even_sector_basis(n, ne).toarray()
+        nsn = math.comb(n, ne)
+        assert Q.shape == (nsn * nsn, nsn * (nsn + 1) // 2)
+        assert np.abs(Q.T @ Q - np.eye(Q.shape[1])).max() < 1e-15
+        p = _swap(nsn)
+        assert np.abs(Q[p] - Q).max() < 1e-15
+    # an even-ground space: both readings agree (dense and sparse paths)
+    h1, eri, occ, _ = hubbard_ring_momentum(8, 1.0, 4.0)
+    for A in ([0, 1, 2, 3, 4, 5], list(range(8))):
+        k = omb.n_active_electrons(occ, A)
+        _, he, ea = omb.frozen_core(h1, eri, occ, A)
+        assert abs(f.lowest_eigenvalue_even(he, ea, k) - f.lowest_eigenvalue(he, ea, k, k)) < 1e-9
