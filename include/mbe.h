@@ -77,10 +77,18 @@ typedef struct mbe_opts {
     double tol_switch;    /* mixed mode: float32 phase ends at this residual         */
     int max_iter;         /* cap on Davidson iterations per phase                    */
     int fp64_final_iters; /* mixed mode: minimum float64 iterations                  */
+    int sectors;          /* MBE_SECTORS_BOTH: the lowest state of the determinant
+                             space; MBE_SECTORS_EVEN: the lowest state that is even
+                             under the exchange of the alpha and beta strings (the
+                             closed-shell determinant's sector; for n_alpha = n_beta
+                             the states of even total spin)                         */
 } mbe_opts;
 
+#define MBE_SECTORS_BOTH 0
+#define MBE_SECTORS_EVEN 1
+
 /* Fills *opts with the defaults: FP64, tol 1e-6, tol_switch 1e-5, max_iter 2000,
-   fp64_final_iters 2.  Host only, synchronous. */
+   fp64_final_iters 2, MBE_SECTORS_BOTH.  Host only, synchronous. */
 void mbe_default_opts(mbe_opts *opts);
 
 /* ------------------------------------------------------------------ context */

@@ -37,7 +37,7 @@ EXPORTS = ("mbe_default_opts", "mbe_ctx_create", "mbe_ctx_set_stream", "mbe_ctx_
 class MbeOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("tol_switch", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("fp64_final_iters", ctypes.c_int)]
+                ("fp64_final_iters", ctypes.c_int), ("sectors", ctypes.c_int)]
 
 
 class MbeTiming(ctypes.Structure):
@@ -137,6 +137,7 @@ class Opts:
     tol_switch: float = 1e-5
     max_iter: int = 2000
     fp64_final_iters: int = 2
+    even_only: bool = False  # only the even sector of the alpha-beta string exchange
 
     def to_c(self) -> MbeOpts:
         o = MbeOpts()
@@ -145,6 +146,7 @@ class Opts:
         o.tol_switch = self.tol_switch
         o.max_iter = self.max_iter
         o.fp64_final_iters = self.fp64_final_iters
+        o.sectors = 1 if self.even_only else 0
         return o
 
 

@@ -63,6 +63,7 @@ struct BatchArgs {
     int precision;
     double tol, tol_switch;
     int max_iter, min_fp64;
+    int even_only;  // solve the even spin-flip sector only
     double *eps;
     int32_t *status;
     int32_t *iters;
@@ -976,7 +977,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
             int n32 = 0, flag = PS_ONE;
             double lam32 = 0.0;
             for (int sector = 0; sector < 2; ++sector) {
-                if (sector == 1 && pb.Ns < 2) break;
+                if (sector == 1 && (pb.Ns < 2 || a.even_only)) break;
                 const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
                 pb.sector = sg.sgn;
                 float x32[DPL];
@@ -1025,7 +1026,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
                 n32 = a.pstate[2 * t + 1];
             }
             for (int sector = 0; sector < 2; ++sector) {
-                if (sector == 1 && (pb.Ns < 2 || status != MBE_STATUS_OK)) break;
+                if (sector == 1 && (pb.Ns < 2 || status != MBE_STATUS_OK || a.even_only)) break;
                 if (MODE == WM_F64 && sector == 1 && flag == PS_ONE) break;
                 const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
                 if (sector == 1 && a.rdm) {
@@ -1678,7 +1679,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
         double lam = 0.0;
         int status = MBE_STATUS_OK, n64 = 0, n32 = 0;
         for (int sector = 0; sector < 2; ++sector) {
-            if (sector == 1 && (pb.Ns < 2 || status != MBE_STATUS_OK)) break;
+            if (sector == 1 && (pb.Ns < 2 || status != MBE_STATUS_OK || a.even_only)) break;
             const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
             if (sector == 1 && a.rdm)
                 for (int d = threadIdx.x; d < pb.N; d += blockDim.x) x2[d] = x64[d];
@@ -1946,7 +1947,8 @@ static int run_casci(mbe_ctx *ctx, int norb, const double *h1, const double *eri
     if (opts) o = *opts; else mbe_default_opts(&o);
     MBE_CHECK(o.precision == MBE_PREC_FP64 || o.precision == MBE_PREC_MIXED, MBE_EINVAL,
               "casci_batch: unknown precision %d", o.precision);
-    MBE_CHECK(o.tol > 0 && o.tol_switch > 0 && o.max_iter >= 1 && o.fp64_final_iters >= 0, MBE_EINVAL,
+    MBE_CHECK(o.tol > 0 && o.tol_switch > 0 && o.max_iter >= 1 && o.fp64_final_iters >= 0 &&
+                  (o.sectors == MBE_SECTORS_BOTH || o.sectors == MBE_SECTORS_EVEN), MBE_EINVAL,
               "casci_batch: bad options");
     if (n_tuples == 0) return MBE_OK;
     MBE_CHECK(rdm || (eps_out != nullptr && status_out != nullptr), MBE_EINVAL, "casci_batch: NULL output");
@@ -1977,6 +1979,7 @@ static int run_casci(mbe_ctx *ctx, int norb, const double *h1, const double *eri
     a.tol_switch = o.tol_switch;
     a.max_iter = o.max_iter;
     a.min_fp64 = o.fp64_final_iters;
+    a.even_only = o.sectors == MBE_SECTORS_EVEN ? 1 : 0;
     a.eps = eps_out;
     a.status = status_out;
     a.iters = iters_out;
@@ -3363,7 +3366,8 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
     if (opts) o = *opts; else mbe_default_opts(&o);
     MBE_CHECK(o.precision == MBE_PREC_FP64 || o.precision == MBE_PREC_MIXED, MBE_EINVAL,
               "casci_solve: unknown precision %d", o.precision);
-    MBE_CHECK(o.tol > 0 && o.tol_switch > 0 && o.max_iter >= 1 && o.fp64_final_iters >= 0, MBE_EINVAL,
+    MBE_CHECK(o.tol > 0 && o.tol_switch > 0 && o.max_iter >= 1 && o.fp64_final_iters >= 0 &&
+                  (o.sectors == MBE_SECTORS_BOTH || o.sectors == MBE_SECTORS_EVEN), MBE_EINVAL,
               "casci_solve: bad options");
     MBE_CU(cudaSetDevice(ctx->device));
     std::vector<uint8_t> occ_h(norb);
@@ -3415,7 +3419,7 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
     // (mixed mode) and the float64 phase; the second sector first runs a float64
     // pass to the residual SECTOR_TOL only and stops there when sector_loses
     for (int sector = 0; sector < 2; ++sector) {
-        if (sector == 1 && (Ns < 2 || st != MBE_STATUS_OK)) break;
+        if (sector == 1 && (Ns < 2 || st != MBE_STATUS_OK || o.sectors == MBE_SECTORS_EVEN)) break;
         const int sgn = sector == 0 ? 1 : -1;
         if (sector == 1) MBE_CU(cudaMemcpyAsync(D.xs, D.x, (size_t)N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
         k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best + sector, Ns, sgn, N, D.x);

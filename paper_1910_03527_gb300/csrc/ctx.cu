@@ -117,6 +117,7 @@ void mbe_default_opts(mbe_opts *o)
     o->tol_switch = 1e-5;
     o->max_iter = 2000;
     o->fp64_final_iters = 2;
+    o->sectors = MBE_SECTORS_BOTH;
 }
 
 const char *mbe_last_error(void) { return g_err; }

@@ -102,3 +102,26 @@ def test_large_solver_finds_the_odd_ground_state(eng, ctx, system, prec):
     res = ctx.casci_solve(dev(h1), dev(eri), dev(occ), list(ODD), eng.Opts(precision=prec, tol=1e-7))
     assert res["status"] == 0
     assert abs(res["lam"] - fci.lowest_eigenvalue(he, ea, k, k)) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_even_sector_targeting(eng, ctx, system, prec):
+    # MBE_SECTORS_EVEN: the lowest state even under the string exchange, against
+    # the oracle's projected eigenproblem; the odd-ground tuples now differ from
+    # the default by the gap to the lowest even state
+    h1, eri, occ = system
+    exp = list(range(8))
+    e_phi = omb.phi_energy(h1, eri, occ)
+    tol = 1e-9 if prec == "fp64" else 1e-8
+    for n in (3, 7):
+        tups = omb.tuples(exp, [], occ, n, True)
+        want = np.array([omb.tuple_energy(h1, eri, occ, [], t, e_phi, 0.0, even_only=True) for t in tups])
+        eps, status, _ = ctx.casci_batch(dev(h1), dev(eri), dev(occ), [], 0.0, n,
+                                         dev(np.array(tups, dtype=np.int32)), eng.Opts(precision=prec, even_only=True))
+        assert int((status != 0).sum()) == 0
+        assert np.abs(eps.cpu().numpy() - want).max() <= tol, n
+    k = omb.n_active_electrons(occ, ODD)
+    _, he, ea = omb.frozen_core(h1, eri, occ, list(ODD))
+    res = ctx.casci_solve(dev(h1), dev(eri), dev(occ), list(ODD), eng.Opts(precision=prec, tol=1e-7, even_only=True))
+    assert res["status"] == 0
+    assert abs(res["lam"] - fci.lowest_eigenvalue_even(he, ea, k)) < 1e-9
