@@ -694,7 +694,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true", help="--large: skip the 12-orbital Davidson solves")
     ap.add_argument("--screened", action="store_true",
                     help="screened expansion (Eq. 4) on a Hubbard ring: tuples per order and solves/s")
-    ap.add_argument("--screened-workload", default="hubbard22", choices=["hubbard22", "hubbard46"])
+    ap.add_argument("--screened-workload", default="hubbard22",
+                    choices=["hubbard22", "hubbard46", "hubbard22pm", "hubbard46pm"])
     ap.add_argument("--screened-max-order", type=int, default=8)
     ap.add_argument("--molecule", action="store_true",
                     help="the synthetic 40-orbital molecule: solves/s per order (block-solver sizes)")

@@ -154,3 +154,35 @@ def test_screened_expansion_matches_oracle(eng, ctx, case, prec):
         assert np.abs(gi - wi).max() <= tol
         assert int((got["status"][k - 1] != 0).sum()) == 0
     assert abs(float(got["e_total"].item()) - want["e_tot"]) <= 10 * tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_screened_expansion_pm_orbitals(eng, ctx, prec):
+    # the Hubbard ring in Pipek-Mezey orbitals (the paper's orbital basis for its
+    # Hubbard runs), where screening removes tuples at orders 5-7
+    from workloads import hubbard_ring_pm
+
+    h1, eri, occ, _ = hubbard_ring_pm(10, 1.0, 4.0)
+    exp = list(range(10))
+    t_init, m_init, a, max_order = 1e-3, 3, 5.0, 7
+    want = omb.run_mbe_screened(h1, eri, occ, [], exp, max_order, True, t_init=t_init, m_init=m_init, a=a)
+    full = {n: omb.tuple_count_closed_form(5, 5, False, False, n, True) for n in want["orders"]}
+    assert sum(len(want["tuples"][n]) for n in want["orders"]) < sum(full.values())
+    for k in want["orders"]:
+        inc = {t: want["inc"][t] for t in want["tuples"][k]}
+        for child in itertools.combinations(exp, k + 1):
+            if not omb.keep_tuple(child, [], occ):
+                continue
+            best = max(abs(inc.get(s, 0.0)) for s in itertools.combinations(child, k))
+            thr = omb.tuple_threshold(child, occ, t_init, m_init, a)
+            assert best == 0.0 or abs(best - thr) > 5e-5
+    got = eng.run_mbe_screened(ctx, dev(h1), dev(eri), dev(occ), [], exp, max_order, True, t_init=t_init,
+                               m_init=m_init, a=a, opts=eng.Opts(precision=prec), occ_host=occ.tolist())
+    assert got["orders"] == want["orders"]
+    tol = 1e-9 if prec == "fp64" else 1e-8
+    for k in want["orders"]:
+        tk = [tuple(int(x) for x in r) for r in got["tuples"][k - 1].cpu().numpy()]
+        assert tk == want["tuples"][k]
+        gi = got["inc"][k - 1].cpu().numpy()
+        assert np.abs(gi - np.array([want["inc"][t] for t in tk])).max() <= tol
+    assert abs(float(got["e_total"].item()) - want["e_tot"]) <= 10 * tol

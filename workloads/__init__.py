@@ -9,6 +9,9 @@ arithmetic (no CASCI, no effective Hamiltonian, no increments).
 from .hamiltonians import (  # noqa: F401
     Workload,
     hubbard_ring_momentum,
+    hubbard_ring_pm,
+    pipek_mezey,
+    pm_functional,
     hubbard_open_dimer,
     synthetic_molecule,
     random_system,

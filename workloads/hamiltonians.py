@@ -127,6 +127,59 @@ def hubbard_ring_momentum(L: int, t: float = 1.0, U: float = 4.0, nocc: Optional
     return np.ascontiguousarray(h1), np.ascontiguousarray(eri), occ, C
 
 
+def pipek_mezey(C: np.ndarray, max_sweeps: int = 500, tol: float = 1e-12) -> np.ndarray:
+    """Pipek-Mezey localisation (Pipek and Mezey, J. Chem. Phys. 90, 4916 (1989))
+    of the orthonormal orbitals in the columns of C, given on an orthonormal
+    site basis: Jacobi sweeps of 2x2 rotations, each at the angle that maximises
+    the sum over orbitals and sites of the squared site populations (C[i, p]^2)^2.
+    For the pair (p, q), with Q_pq = C[:, p] C[:, q] sitewise,
+        A = sum (Q_pq^2 - (Q_pp - Q_qq)^2 / 4),  B = sum Q_pq (Q_pp - Q_qq),
+    the rotation p' = cos g p + sin g q, q' = -sin g p + cos g q with
+    4 g = atan2(B, -A) is optimal.  Deterministic for a given C."""
+    C = np.array(C, dtype=np.float64, copy=True)
+    n = C.shape[1]
+    for _ in range(max_sweeps):
+        biggest = 0.0
+        for p in range(n):
+            for q in range(p + 1, n):
+                cp, cq = C[:, p].copy(), C[:, q].copy()
+                qpq, qpp, qqq = cp * cq, cp * cp, cq * cq
+                A = float(np.sum(qpq * qpq - 0.25 * (qpp - qqq) ** 2))
+                B = float(np.sum(qpq * (qpp - qqq)))
+                if A * A + B * B < 1e-28:
+                    continue
+                g = 0.25 * np.arctan2(B, -A)
+                if abs(g) < 1e-15:
+                    continue
+                c, s = np.cos(g), np.sin(g)
+                C[:, p] = c * cp + s * cq
+                C[:, q] = -s * cp + c * cq
+                biggest = max(biggest, abs(g))
+        if biggest < tol:
+            break
+    return C
+
+
+def pm_functional(C: np.ndarray) -> float:
+    """Sum over orbitals and sites of the squared site populations."""
+    return float(np.sum(C ** 4))
+
+
+def hubbard_ring_pm(L: int, t: float = 1.0, U: float = 4.0, nocc: Optional[int] = None):
+    """Periodic Hubbard ring in Pipek-Mezey orbitals: the momentum orbitals of the
+    occupied and of the virtual space localised separately (the reference
+    determinant is unchanged). Returns (h1, eri, occ, C)."""
+    h1m, erim, occ, Cm = hubbard_ring_momentum(L, t, U, nocc)
+    no = int(occ.sum())
+    C = np.concatenate([pipek_mezey(Cm[:, :no]), pipek_mezey(Cm[:, no:])], axis=1)
+    hs, _ = hubbard_site_integrals(L, t, U, periodic=True)
+    h1 = C.T @ hs @ C
+    h1 = 0.5 * (h1 + h1.T)
+    eri = U * np.einsum("ip,iq,ir,is->pqrs", C, C, C, C, optimize=True)
+    _check(h1, eri)
+    return np.ascontiguousarray(h1), np.ascontiguousarray(eri), occ, C
+
+
 def hubbard_open_dimer(t: float = 1.0, U: float = 4.0):
     """Two sites joined by one bond (no ring), in the site basis; site 0 occupied."""
     h1, eri = hubbard_site_integrals(2, t, U, periodic=False)
@@ -217,7 +270,7 @@ def block_decoupled_system(n1: int, nocc1: int, n2: int, nocc2: int, seed: int,
     return h1, eri, occ, block
 
 
-WORKLOAD_NAMES = ("hubbard8", "hubbard22", "molecule40", "hubbard46", "molecule20")
+WORKLOAD_NAMES = ("hubbard8", "hubbard22", "molecule40", "hubbard46", "molecule20", "hubbard22pm", "hubbard46pm")
 
 
 def workload(name: str) -> Workload:
@@ -243,6 +296,11 @@ def workload(name: str) -> Workload:
         h1, eri, occ, _ = hubbard_ring_momentum(22, 1.0, 4.0)
         return Workload(name, h1, eri, occ, [], list(range(22)), list(range(1, 7)), True,
                         "Hubbard ring L=22 t=1 U=4, orders 1-6", dict(L=22, t=1.0, U=4.0))
+    if name in ("hubbard22pm", "hubbard46pm"):
+        L = 22 if name == "hubbard22pm" else 46
+        h1, eri, occ, _ = hubbard_ring_pm(L, 1.0, 4.0)
+        return Workload(name, h1, eri, occ, [], list(range(L)), list(range(1, 7 if L == 22 else 5)), True,
+                        f"Hubbard ring L={L} t=1 U=4, Pipek-Mezey orbitals", dict(L=L, t=1.0, U=4.0))
     if name == "hubbard46":
         h1, eri, occ, _ = hubbard_ring_momentum(46, 1.0, 4.0)
         return Workload(name, h1, eri, occ, [], list(range(46)), list(range(1, 5)), True,
