@@ -8,12 +8,14 @@ increments -> totals).
 """
 
 from .binding import (  # noqa: F401
+    EXPANSION_TYPES,
     EXPORTS,
     Context,
     MBEEnergy,
     MbeError,
     Opts,
     STATUS_NAMES,
+    expansion_spaces,
     lib,
     library_path,
     mbe_gradient,

@@ -454,6 +454,46 @@ class MBEEnergy(torch.autograd.Function):
         return g * gh, (g * ge if ge is not None else None), None, None, None, None, None, None, None, None
 
 
+EXPANSION_TYPES = ("type1", "type2", "type3")
+
+
+def expansion_spaces(occ: Sequence[int], kind: str, active: Sequence[int] = ()):
+    """(ref, exp) of the three expansion types of Sec. 1 (Fig. 1), as sorted lists.
+
+    * type1 (Bethe-Goldstone): the expansion space is the occupied orbitals, and
+      the reference space is every virtual orbital, so an order-k tuple
+      correlates 2k electrons in k + M_vir orbitals.  `active` must be empty.
+    * type2: the reference space is every occupied orbital plus the virtual
+      orbitals in `active`; the expansion space is the other virtuals.  Every
+      tuple correlates all electrons.
+    * type3: the reference space is `active` (empty: the vacuum reference
+      space); the expansion space is every other orbital.
+
+    Host-side choice of orbital lists only; run_mbe and run_mbe_screened take
+    the result as their ref and exp.  Raises ValueError on an unknown kind, on
+    an orbital index out of range or repeated, on occupied orbitals in a type2
+    `active`, and on a type1 call with a non-empty `active`.
+    """
+    occ_h = [int(v) for v in occ]
+    norb = len(occ_h)
+    act = sorted(int(p) for p in active)
+    if kind not in EXPANSION_TYPES:
+        raise ValueError(f"expansion_spaces: kind must be one of {EXPANSION_TYPES}, got {kind!r}")
+    if any(p < 0 or p >= norb for p in act) or len(set(act)) != len(act):
+        raise ValueError("expansion_spaces: active orbitals out of range or repeated")
+    occupied = [p for p in range(norb) if occ_h[p]]
+    virtual = [p for p in range(norb) if not occ_h[p]]
+    if kind == "type1":
+        if act:
+            raise ValueError("expansion_spaces: type1 takes no active orbitals")
+        return virtual, occupied
+    if kind == "type2":
+        if any(occ_h[p] for p in act):
+            raise ValueError("expansion_spaces: type2 active orbitals must be virtual")
+        return sorted(occupied + act), [p for p in virtual if p not in act]
+    return act, [p for p in range(norb) if p not in act]
+
+
 def run_mbe(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequence[int],
             orders: Sequence[int], skip: bool, opts: Optional[Opts] = None,
             occ_host: Optional[Sequence[int]] = None):

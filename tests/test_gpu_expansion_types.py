@@ -1,0 +1,116 @@
+"""Parity of Type-1 and Type-2 expansions (Sec. 1, Fig. 1) against the oracle.
+
+Type-1 expands in the occupied orbitals with every virtual in the reference
+space; Type-2 expands in the virtuals with every occupied orbital (and, in the
+third case, one active virtual) in the reference space.  The spaces come from
+expansion_spaces; the GPU path is run_mbe (tuples, tuple CASCI, increments and
+totals, all through the C ABI) and the screened run_mbe_screened.  The tuple
+active spaces run from 16 determinants (warp solver) to 3136 (block solver),
+the last order being the full space, so the totals must also equal FCI.
+"""
+
+import itertools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle import fci, mbe as omb  # noqa: E402
+from workloads import random_system  # noqa: E402
+
+CASES = {"type1": ("type1", ()), "type2": ("type2", ()), "type2_active": ("type2", (3,))}
+TOL = {"fp64": 1e-9, "mixed": 1e-8}
+
+
+@pytest.fixture(scope="module")
+def eng():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1910_03527_gb300 as e
+    e.build()
+    return e
+
+
+@pytest.fixture(scope="module")
+def ctx(eng):
+    c = eng.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def system():
+    h1, eri, occ = random_system(8, 3, seed=51)
+    return h1, eri, occ, fci.lowest_eigenvalue(h1, eri, 3, 3)
+
+
+_oracle_cache = {}
+
+
+def oracle_run(system, case):
+    if case not in _oracle_cache:
+        from paper_1910_03527_gb300.binding import expansion_spaces
+        h1, eri, occ, _ = system
+        ref, exp = expansion_spaces(occ, *CASES[case])
+        _oracle_cache[case] = (ref, exp, omb.run_mbe(h1, eri, occ, ref, exp, list(range(1, len(exp) + 1)), True))
+    return _oracle_cache[case]
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_expansion_type_matches_oracle(eng, ctx, system, case, prec):
+    h1, eri, occ, fci_e = system
+    ref, exp, want = oracle_run(system, case)
+    orders = list(range(1, len(exp) + 1))
+    got = eng.run_mbe(ctx, dev(h1), dev(eri), dev(occ), ref, exp, orders, True, eng.Opts(precision=prec),
+                      occ_host=occ.tolist())
+    tol = TOL[prec]
+    assert abs(got["e_ref_corr"] - want["e_ref_corr"]) <= tol
+    for i, n in enumerate(orders):
+        tk = [tuple(int(x) for x in r) for r in got["tuples"][i].cpu().numpy()]
+        assert tk == omb.tuples(exp, ref, occ, n, True)
+        assert int((got["status"][i] != 0).sum()) == 0
+        eps = got["eps"][i].cpu().numpy()
+        assert np.abs(eps - np.array([want["eps"][n][t] for t in tk])).max() <= tol, n
+        inc = got["inc"][i].cpu().numpy()
+        assert np.abs(inc - np.array([want["inc"][t] for t in tk])).max() <= 4 * tol, n
+    e_order = got["e_order"].cpu().numpy()
+    for i, n in enumerate(orders):
+        assert abs(e_order[i] - want["e_order"][n]) <= 16 * tol
+    assert abs(float(got["e_total"].item()) - want["e_tot"]) <= 32 * tol
+    assert abs(float(got["e_total"].item()) - fci_e) <= 32 * tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_screened_type2_matches_oracle(eng, ctx, system, prec):
+    from paper_1910_03527_gb300.binding import expansion_spaces
+    h1, eri, occ, _ = system
+    ref, exp = expansion_spaces(occ, "type2")
+    # Type-2 tuples hold only virtuals, so M_tup of Eq. 4 is the tuple's order; these
+    # thresholds drop one order-4 tuple and the order-5 one
+    t_init, m_init, a, max_order = 1.5e-2, 3, 1.5, 5
+    want = omb.run_mbe_screened(h1, eri, occ, ref, exp, max_order, True, t_init=t_init, m_init=m_init, a=a)
+    assert want["orders"] == [1, 2, 3, 4] and len(want["tuples"][4]) == 4
+    for k in want["orders"]:
+        inc = {t: want["inc"][t] for t in want["tuples"][k]}
+        for child in itertools.combinations(exp, k + 1):
+            best = max(abs(inc.get(s, 0.0)) for s in itertools.combinations(child, k))
+            thr = omb.tuple_threshold(child, occ, t_init, m_init, a)
+            assert best == 0.0 or abs(best - thr) > 1e-5
+    got = eng.run_mbe_screened(ctx, dev(h1), dev(eri), dev(occ), ref, exp, max_order, True, t_init=t_init,
+                               m_init=m_init, a=a, opts=eng.Opts(precision=prec), occ_host=occ.tolist())
+    assert got["orders"] == want["orders"]
+    tol = TOL[prec]
+    for k in want["orders"]:
+        tk = [tuple(int(x) for x in r) for r in got["tuples"][k - 1].cpu().numpy()]
+        assert tk == want["tuples"][k]
+        gi = got["inc"][k - 1].cpu().numpy()
+        assert np.abs(gi - np.array([want["inc"][t] for t in tk])).max() <= 4 * tol
+    assert abs(float(got["e_total"].item()) - want["e_tot"]) <= 32 * tol
