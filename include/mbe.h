@@ -350,6 +350,32 @@ int casci_sigma_large(mbe_ctx *ctx, int norb, const double *h1, const double *er
 int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ, int n_cas,
                 const int32_t *cas_orbs, const mbe_opts *opts, double *result, int32_t *info, double *cvec);
 
+/*
+ * casci_batch for the large tuple active spaces of Type-1 and Type-2 expansions
+ * (Sec. 1, Fig. 1: a reference space of every virtual, or of every occupied
+ * orbital, so that |R u Omega| grows to the sizes of a single big CASCI).  Same
+ * arguments, output and meaning as casci_batch (eps_out[t] = E_CAS(R u tuple_t)
+ * - E_Phi - e_ref_corr), with |R| + order up to MBE_MAX_LARGE_CAS and one more:
+ *   large_ndet   a tuple whose active space has more than large_ndet determinants
+ *                (large_ndet > 0), or more than MBE_MAX_CAS orbitals, is solved by
+ *                casci_solve with the whole GPU; the others go to casci_batch in
+ *                one call (gathered to a temporary list when the order is mixed).
+ *                With large_ndet <= 0 and |R| + order <= MBE_MAX_CAS this is
+ *                casci_batch itself.
+ * A routed tuple's iters_out holds casci_solve's sigma counts in the casci_batch
+ * encoding; a routed active space with one determinant (Phi_A) gets eps =
+ * -e_ref_corr without a solve.  Synchronous when any tuple is routed (the host
+ * reads the tuples and occupations, and casci_solve is synchronous); temporary
+ * device buffers are stream-ordered allocations freed before return.
+ * Errors: as casci_batch and casci_solve; MBE_EUNSUPPORTED for |R| + order
+ * above MBE_MAX_LARGE_CAS.  A malformed routed tuple gets MBE_STATUS_BADINPUT
+ * and eps NaN, as in casci_batch.
+ */
+int casci_batch_routed(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
+                       int n_ref, const int32_t *ref_orbs, double e_ref_corr, int order, int64_t n_tuples,
+                       const int32_t *tuples, const mbe_opts *opts, int64_t large_ndet, double *eps_out,
+                       int32_t *status_out, int32_t *iters_out);
+
 /* ------------------------------------------------------------------ screened expansion */
 
 /*

@@ -24,6 +24,7 @@ MBE_PREC_FP64 = 0
 MBE_PREC_MIXED = 1
 MBE_SKIP_NO_OCC_OR_VIRT = 1
 MBE_MAX_CAS = 12
+MBE_MAX_LARGE_CAS = 16
 STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "NONFINITE", 3: "BADINPUT"}
 
 EXPORTS = ("mbe_default_opts", "mbe_ctx_create", "mbe_ctx_set_stream", "mbe_ctx_destroy",
@@ -31,7 +32,7 @@ EXPORTS = ("mbe_default_opts", "mbe_ctx_create", "mbe_ctx_set_stream", "mbe_ctx_
            "mbe_ctx_timings", "mbe_tuples", "mbe_string_table", "mbe_phi_energy",
            "casci_batch", "casci_sigma", "casci_sigma_noalloc", "mbe_increments", "mbe_total",
            "mbe_weights", "casci_rdm_batch", "mbe_phi_gradient", "casci_sigma_large", "casci_solve",
-           "mbe_screen")
+           "mbe_screen", "casci_batch_routed")
 
 
 class MbeOpts(ctypes.Structure):
@@ -107,6 +108,9 @@ def lib() -> ctypes.CDLL:
     L.casci_sigma_large.argtypes = [P, i32, P, P, P, i32, P, i32, P, P, P]
     L.casci_solve.restype = i32
     L.casci_solve.argtypes = [P, i32, P, P, P, i32, P, ctypes.POINTER(MbeOpts), P, P, P]
+    L.casci_batch_routed.restype = i32
+    L.casci_batch_routed.argtypes = [P, i32, P, P, P, i32, P, dbl, i32, i64, P, ctypes.POINTER(MbeOpts), i64,
+                                     P, P, P]
     L.mbe_screen.restype = i32
     L.mbe_screen.argtypes = [P, i32, P, i32, P, i32, P, i32, i64, P, P, dbl, i32, dbl, i32, i64,
                              ctypes.POINTER(i64), P]
@@ -286,6 +290,27 @@ class Context:
                                  self._p(self._dev(occ, torch.uint8, "occ")), len(ref), ref_h,
                                  float(e_ref_corr), order, n_t, self._p(tuples), ctypes.byref(o),
                                  self._p(eps), self._p(status), self._p(iters)), "casci_batch")
+        return eps, status, iters
+
+    def casci_batch_routed(self, h1, eri, occ, ref: Sequence[int], e_ref_corr: float, order: int,
+                           tuples: Optional[torch.Tensor], opts: Optional[Opts] = None, large_ndet: int = 0):
+        """casci_batch for active spaces of up to MBE_MAX_LARGE_CAS orbitals: tuples above
+        MBE_MAX_CAS orbitals or above large_ndet determinants (if > 0) are solved one at a
+        time with the whole GPU."""
+        norb = h1.shape[0]
+        if tuples is not None:
+            self._dev(tuples, torch.int32, "tuples")
+        n_t = tuples.shape[0] if tuples is not None else 1
+        eps = self._empty((n_t,), torch.float64)
+        status = self._empty((n_t,), torch.int32)
+        iters = self._empty((n_t,), torch.int32)
+        o = (opts or Opts()).to_c()
+        _check(lib().casci_batch_routed(self._h, norb, self._p(self._dev(h1, torch.float64, "h1")),
+                                        self._p(self._dev(eri, torch.float64, "eri")),
+                                        self._p(self._dev(occ, torch.uint8, "occ")), len(ref), _i32_host(ref),
+                                        float(e_ref_corr), order, n_t, self._p(tuples), ctypes.byref(o),
+                                        int(large_ndet), self._p(eps), self._p(status), self._p(iters)),
+               "casci_batch_routed")
         return eps, status, iters
 
     def casci_sigma(self, h1, eri, occ, cas: Sequence[int], c: torch.Tensor, want_diag: bool = True):
@@ -494,27 +519,38 @@ def expansion_spaces(occ: Sequence[int], kind: str, active: Sequence[int] = ()):
     return act, [p for p in range(norb) if p not in act]
 
 
+def _order_casci(ctx: Context, h1, eri, occ, ref, e_ref, order, tup, opts, large_ndet):
+    """casci_batch, or casci_batch_routed when the active spaces exceed MBE_MAX_CAS
+    orbitals or a determinant limit for the batched solvers is given."""
+    if len(ref) + order <= MBE_MAX_CAS and not large_ndet:
+        return ctx.casci_batch(h1, eri, occ, ref, e_ref, order, tup, opts)
+    return ctx.casci_batch_routed(h1, eri, occ, ref, e_ref, order, tup, opts, large_ndet or 0)
+
+
 def run_mbe(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequence[int],
             orders: Sequence[int], skip: bool, opts: Optional[Opts] = None,
-            occ_host: Optional[Sequence[int]] = None):
+            occ_host: Optional[Sequence[int]] = None, large_ndet: Optional[int] = None):
     """One pass of the whole hot path through the C ABI: tuples, tuple CASCI,
     increments (Eq. 2) and the order sums and total (Eq. 1), all on the device.
 
     h1, eri, occ are device tensors.  Returns a dict of device tensors (per-order
     tuples, eps, status, iters, increments; e_order, e_total, e_phi) and the
-    reference-space correlation energy used.
+    reference-space correlation energy used.  Active spaces R u Omega of more than
+    MBE_MAX_CAS (up to MBE_MAX_LARGE_CAS) orbitals, as in Type-1 and Type-2
+    expansions, and with large_ndet set the tuples above that many determinants,
+    go through casci_batch_routed.
     """
     occ_h = [int(v) for v in (occ_host if occ_host is not None else occ.cpu().tolist())]
     norb = h1.shape[0]
     e_phi = ctx.mbe_phi_energy(h1, eri, occ)
     e_ref = 0.0
     if len(ref) > 0:
-        eps_r, st_r, _ = ctx.casci_batch(h1, eri, occ, ref, 0.0, 0, None, opts)
+        eps_r, st_r, _ = _order_casci(ctx, h1, eri, occ, ref, 0.0, 0, None, opts, large_ndet)
         e_ref = float(eps_r.item())
     out = dict(tuples=[], eps=[], status=[], iters=[], inc=[], e_phi=e_phi, e_ref_corr=e_ref)
     for n in orders:
         tup = ctx.mbe_tuples(norb, occ_h, exp, ref, n, skip)
-        eps, status, iters = ctx.casci_batch(h1, eri, occ, ref, e_ref, n, tup, opts)
+        eps, status, iters = _order_casci(ctx, h1, eri, occ, ref, e_ref, n, tup, opts, large_ndet)
         inc = ctx.mbe_increments(n, tup, eps, out["tuples"], out["inc"]) if n == len(out["inc"]) + 1 \
             else None
         if inc is None:
@@ -532,7 +568,8 @@ def run_mbe(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequence[int],
 
 def run_mbe_screened(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequence[int], max_order: int,
                      skip: bool, t_init: float = 1e-10, m_init: int = 3, a: float = 5.0,
-                     opts: Optional[Opts] = None, occ_host: Optional[Sequence[int]] = None):
+                     opts: Optional[Opts] = None, occ_host: Optional[Sequence[int]] = None,
+                     large_ndet: Optional[int] = None):
     """The screened expansion through the C ABI: orders up to the first computed
     one (order 2 for an empty reference space with the skip rule, else 1) are
     complete; every later order holds the children mbe_screen spawns from the
@@ -543,7 +580,7 @@ def run_mbe_screened(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequen
     e_phi = ctx.mbe_phi_energy(h1, eri, occ)
     e_ref = 0.0
     if len(ref) > 0:
-        eps_r, st_r, _ = ctx.casci_batch(h1, eri, occ, ref, 0.0, 0, None, opts)
+        eps_r, st_r, _ = _order_casci(ctx, h1, eri, occ, ref, 0.0, 0, None, opts, large_ndet)
         e_ref = float(eps_r.item())
     k0 = 2 if (skip and len(ref) == 0) else 1
     out = dict(tuples=[], eps=[], status=[], iters=[], inc=[], e_phi=e_phi, e_ref_corr=e_ref, orders=[])
@@ -555,7 +592,7 @@ def run_mbe_screened(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequen
                                  t_init, m_init, a, skip)
         if tup.shape[0] == 0 and n >= k0:
             break
-        eps, status, iters = ctx.casci_batch(h1, eri, occ, ref, e_ref, n, tup, opts)
+        eps, status, iters = _order_casci(ctx, h1, eri, occ, ref, e_ref, n, tup, opts, large_ndet)
         inc = ctx.mbe_increments(n, tup, eps, out["tuples"], out["inc"])
         out["tuples"].append(tup)
         out["eps"].append(eps)

@@ -127,3 +127,19 @@ def test_hubbard_type1_and_type2_reach_fci():
         assert abs(res["e_tot"] - fci_e) < 1e-9
         assert all(len(t) <= 3 for t in res["inc"])
         assert len(res["inc"]) == sum(math.comb(3, k) for k in range(1, 4))
+
+
+def test_decoupled_blocks_cas_energy_is_the_sum_over_blocks():
+    # The reading the large-active-space GPU test takes its expected values from:
+    # with h and (pq|rs) zero across two blocks (and a gap that keeps each block's
+    # electron count), E_CAS(A) - E_Phi is the sum over the blocks of the CASCI of
+    # A's part in that block, the other block frozen.
+    from workloads import block_decoupled_system
+
+    h, eri, occ, block = block_decoupled_system(4, 2, 4, 2, seed=8)
+    e_phi = mbe.phi_energy(h, eri, occ)
+    ref, exp = expansion_spaces(occ, "type2", active=[4, 5])
+    for A in (ref, sorted(ref + [6]), sorted(ref + [7]), list(range(8))):
+        direct = mbe.casci_energy(h, eri, occ, A) - e_phi
+        split = sum(mbe.casci_energy(h, eri, occ, [p for p in A if block[p] == b]) - e_phi for b in (0, 1))
+        assert abs(direct - split) < 1e-10

@@ -114,3 +114,67 @@ def test_screened_type2_matches_oracle(eng, ctx, system, prec):
         gi = got["inc"][k - 1].cpu().numpy()
         assert np.abs(gi - np.array([want["inc"][t] for t in tk])).max() <= 4 * tol
     assert abs(float(got["e_total"].item()) - want["e_tot"]) <= 32 * tol
+
+
+@pytest.mark.parametrize("case,large_ndet", [("type1", 100), ("type2", 200)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_routed_tuples_match_oracle(eng, ctx, system, case, large_ndet, prec):
+    # tuples above large_ndet determinants (441 and 3136 for Type-1, 400 to 3136 for
+    # Type-2) are solved one at a time by casci_solve; the rest by casci_batch
+    h1, eri, occ, fci_e = system
+    ref, exp, want = oracle_run(system, case)
+    orders = list(range(1, len(exp) + 1))
+    got = eng.run_mbe(ctx, dev(h1), dev(eri), dev(occ), ref, exp, orders, True, eng.Opts(precision=prec),
+                      occ_host=occ.tolist(), large_ndet=large_ndet)
+    tol = TOL[prec]
+    n_routed = 0
+    for i, n in enumerate(orders):
+        tk = [tuple(int(x) for x in r) for r in got["tuples"][i].cpu().numpy()]
+        assert int((got["status"][i] != 0).sum()) == 0
+        assert int((got["iters"][i] <= 0).sum()) == 0 or n == 1
+        eps = got["eps"][i].cpu().numpy()
+        assert np.abs(eps - np.array([want["eps"][n][t] for t in tk])).max() <= tol, n
+        n_routed += sum(1 for t in tk if _ndet(occ, ref, t) > large_ndet)
+    assert n_routed >= 2
+    assert abs(float(got["e_total"].item()) - fci_e) <= 32 * tol
+
+
+def _ndet(occ, ref, t):
+    import math
+    A = list(ref) + list(t)
+    k = sum(int(occ[p]) for p in A)
+    return math.comb(len(A), k) ** 2
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_active_spaces_beyond_the_batched_limit(eng, ctx, prec):
+    # Two decoupled 7-orbital blocks (3 occupied each, interleaved): Type-2 with six
+    # active virtuals puts 12 orbitals in R, so every tuple's active space (13 and 14
+    # orbitals, up to 9,018,009 determinants) is beyond casci_batch's 12.  The exact
+    # eps of an active space A is the sum over blocks of the oracle CASCI of A's part
+    # in that block; the cross-block order-2 increment vanishes, and the full-order
+    # total is the sum of the blocks' FCI energies.
+    from workloads import block_decoupled_system
+
+    h1, eri, occ, block = block_decoupled_system(7, 3, 7, 3, seed=8)
+    ref, exp = eng.expansion_spaces(occ, "type2", active=list(range(6, 12)))
+    assert len(ref) == 12 and exp == [12, 13] and block[12] != block[13]
+    e_phi = omb.phi_energy(h1, eri, occ)
+
+    def e_cas_minus_phi(A):
+        return sum(omb.casci_energy(h1, eri, occ, [p for p in A if block[p] == b]) - e_phi for b in (0, 1))
+
+    e_ref = e_cas_minus_phi(ref)
+    want = {t: e_cas_minus_phi(sorted(ref + list(t))) - e_ref for t in [(12,), (13,), (12, 13)]}
+    got = eng.run_mbe(ctx, dev(h1), dev(eri), dev(occ), ref, exp, [1, 2], True, eng.Opts(precision=prec),
+                      occ_host=occ.tolist(), large_ndet=100000)
+    tol = TOL[prec]
+    assert abs(got["e_ref_corr"] - e_ref) <= tol
+    for i, n in enumerate([1, 2]):
+        assert int((got["status"][i] != 0).sum()) == 0
+        tk = [tuple(int(x) for x in r) for r in got["tuples"][i].cpu().numpy()]
+        eps = got["eps"][i].cpu().numpy()
+        assert np.abs(eps - np.array([want[t] for t in tk])).max() <= tol
+    assert abs(float(got["inc"][1][0].item())) <= 4 * tol
+    fci_blocks = e_phi + e_cas_minus_phi(list(range(14)))
+    assert abs(float(got["e_total"].item()) - fci_blocks) <= 32 * tol
