@@ -143,3 +143,16 @@ def test_decoupled_blocks_cas_energy_is_the_sum_over_blocks():
         direct = mbe.casci_energy(h, eri, occ, A) - e_phi
         split = sum(mbe.casci_energy(h, eri, occ, [p for p in A if block[p] == b]) - e_phi for b in (0, 1))
         assert abs(direct - split) < 1e-10
+
+
+@pytest.mark.parametrize("L,U", [(6, 2.0), (10, 4.0)])
+def test_particle_hole_symmetry_makes_type1_equal_type2_on_the_half_filled_ring(L, U):
+    # An even ring is bipartite, so at half filling the particle-hole map (which
+    # sends the momentum orbital k to k + pi, occupied to virtual) is a symmetry of
+    # H: the Type-1 and Type-2 expansions are mirror images and agree at every
+    # truncation order.
+    h, eri, occ, _ = hubbard_ring_momentum(L, 1.0, U)
+    for kmax in (1, 2):
+        e = [mbe.run_mbe(h, eri, occ, *expansion_spaces(occ, kind), list(range(1, kmax + 1)), True)["e_tot"]
+             for kind in ("type1", "type2")]
+        assert abs(e[0] - e[1]) < 1e-12
