@@ -156,3 +156,27 @@ def test_particle_hole_symmetry_makes_type1_equal_type2_on_the_half_filled_ring(
         e = [mbe.run_mbe(h, eri, occ, *expansion_spaces(occ, kind), list(range(1, kmax + 1)), True)["e_tot"]
              for kind in ("type1", "type2")]
         assert abs(e[0] - e[1]) < 1e-12
+
+
+def test_run_mbe_routes_large_active_spaces():
+    # host-side choice between casci_batch and casci_batch_routed (no GPU: a fake
+    # context records which entry point each order would call)
+    from paper_1910_03527_gb300.binding import _order_casci
+
+    class Fake:
+        def __init__(self):
+            self.calls = []
+
+        def casci_batch(self, h1, eri, occ, ref, e_ref, order, tup, opts):
+            self.calls.append(("batch", len(ref) + order))
+
+        def casci_batch_routed(self, h1, eri, occ, ref, e_ref, order, tup, opts, large_ndet):
+            self.calls.append(("routed", len(ref) + order, large_ndet))
+
+    f = Fake()
+    ref = list(range(11))
+    for order in (0, 1, 2, 5):
+        _order_casci(f, None, None, None, ref, 0.0, order, None, None, None)
+    _order_casci(f, None, None, None, ref[:4], 0.0, 2, None, None, 5000)
+    assert f.calls == [("batch", 11), ("batch", 12), ("routed", 13, 0), ("routed", 16, 0),
+                       ("routed", 6, 5000)]
