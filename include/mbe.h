@@ -45,7 +45,8 @@ extern "C" {
 
 /* Compiled limits. */
 #define MBE_MAX_NORB 64       /* orbitals in the full space                    */
-#define MBE_MAX_CAS 12        /* orbitals in one tuple active space |R u Omega| */
+#define MBE_MAX_CAS 12        /* orbitals in one tuple active space |R u Omega| of
+                                 casci_batch (casci_batch_routed: MBE_MAX_LARGE_CAS) */
 #define MBE_MAX_ORDER 16      /* tuple order n                                 */
 #define MBE_MAX_STRING_ORB 16 /* orbitals of one string table (mbe_string_table) */
 
