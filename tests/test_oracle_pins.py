@@ -90,6 +90,50 @@ def test_sigma_and_diagonal_match_dense():
     assert np.allclose(H, H.T, atol=1e-14)
 
 
+# sigma_rows is the only checker of the GPU sigma above 50k determinants, so it is
+# pinned here twice: against H c from the Fock-space Hamiltonian (fermion operator
+# matrices, no Slater-Condon case analysis, no determinant addressing of the oracle),
+# and against the column-driven oracle sigma on larger sectors.  Sectors include
+# na != nb, empty and full spin strings, and every row as well as random subsets
+# (a wrong row-to-determinant mapping or a dropped connection class fails).
+@pytest.mark.parametrize("n,na,nb,seed", [(2, 1, 1, 0), (3, 1, 2, 1), (4, 2, 2, 2), (4, 0, 2, 3),
+                                          (4, 4, 1, 4), (5, 2, 3, 5), (5, 3, 3, 6), (5, 5, 0, 7)])
+def test_sigma_rows_equals_fock_space_h_times_c(n, na, nb, seed):
+    h, eri, _ = random_system(n, max(na, nb), seed=seed)
+    H_ref, words = sector_matrix(h, eri, na, nb)
+    c = np.random.default_rng(seed).normal(size=len(words))
+    want = H_ref @ c
+    rows = np.arange(len(words))
+    got = fci.sigma_rows(h, eri, na, nb, c, rows)
+    np.testing.assert_allclose(got, want, atol=1e-12 * max(1.0, np.abs(want).max()), rtol=0)
+    sub = np.random.default_rng(seed + 100).permutation(len(words))[: max(1, len(words) // 3)]
+    got_sub = fci.sigma_rows(h, eri, na, nb, c, sub)
+    np.testing.assert_allclose(got_sub, want[sub], atol=1e-12 * max(1.0, np.abs(want).max()), rtol=0)
+
+
+@pytest.mark.parametrize("n,na,nb,seed", [(6, 3, 3, 11), (7, 2, 4, 12), (8, 4, 4, 13), (8, 1, 7, 14),
+                                          (8, 3, 2, 15)])
+def test_sigma_rows_equals_oracle_sigma(n, na, nb, seed):
+    h, eri, _ = random_system(n, max(na, nb), seed=seed)
+    N = fci.binom(n, na) * fci.binom(n, nb)
+    c = np.random.default_rng(seed).normal(size=N)
+    want = fci.sigma(h, eri, na, nb, c)
+    got = fci.sigma_rows(h, eri, na, nb, c, np.arange(N))
+    scale = np.abs(want).max()
+    np.testing.assert_allclose(got, want, atol=1e-12 * scale, rtol=0)
+    rows = np.random.default_rng(seed + 1).choice(N, size=min(N, 97), replace=False)
+    np.testing.assert_allclose(fci.sigma_rows(h, eri, na, nb, c, rows), want[rows], atol=1e-12 * scale,
+                               rtol=0)
+    # a single unit vector: column j of H, against the dense Slater-Condon matrix of another route
+    if N <= 1500:
+        H = fci.h_dense(h, eri, na, nb)
+        j = int(np.argmax(np.abs(c)))
+        e = np.zeros(N)
+        e[j] = 1.0
+        np.testing.assert_allclose(fci.sigma_rows(h, eri, na, nb, e, np.arange(N)), H[:, j], atol=1e-13,
+                                   rtol=0)
+
+
 # ----------------------------------------------------------------------------- closed forms
 
 @pytest.mark.parametrize("t,U", [(1.0, 0.0), (1.0, 2.0), (1.0, 4.0), (0.5, 3.0), (2.0, 1.0)])
