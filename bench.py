@@ -170,9 +170,11 @@ def recorded_traffic(kernel_key: str):
 
 # ----------------------------------------------------------------------------- oracle leg
 
-def oracle_sample(seconds: float, seed: int = 1910):
+def oracle_sample(seconds: float, seed: int = 1910, shard: int = 0, nshards: int = 1):
     """Oracle tuple CASCIs on a seeded sample of the workload, stratified by order
-    in proportion to the tuple counts, for about `seconds` of single-core work."""
+    in proportion to the tuple counts, for about `seconds` of single-core work.
+    With nshards > 1 this process takes every nshards-th tuple of the same
+    stratified sequence, starting at `shard`."""
     import numpy as np
     from oracle import mbe as omb
     from workloads import workload
@@ -189,6 +191,7 @@ def oracle_sample(seconds: float, seed: int = 1910):
             idx = rng.permutation(len(lists[n]))
             seq += [(len(lists[n]) / total, i / len(lists[n]), n, lists[n][j]) for i, j in enumerate(idx)]
     seq.sort(key=lambda x: x[1])
+    seq = seq[shard::nshards]
     t0 = time.perf_counter()
     done = 0
     per_order = {}
@@ -202,22 +205,53 @@ def oracle_sample(seconds: float, seed: int = 1910):
     return {"tuples": done, "seconds": dt, "per_order": per_order}
 
 
-def run_oracle_subprocess(seconds: float):
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_subprocess(seconds: float, nproc: int = 1):
+    """The oracle sample in `nproc` single-threaded processes at once (one per
+    host core), each on its own share of the stratified sequence; the rate is
+    the tuples of all processes over the wall time of the slowest."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(seconds)],
-                         capture_output=True, text=True, env=env, cwd=ROOT, timeout=seconds * 4 + 120)
-    if out.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    procs = []
+    t0 = time.perf_counter()
+    for i in range(nproc):
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(seconds),
+               "--oracle-shard", str(i), "--oracle-shards", str(nproc)]
+        procs.append(subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env,
+                                      cwd=ROOT))
+    res = []
+    for p in procs:
+        out, err = p.communicate(timeout=seconds * 4 + 180)
+        if p.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    wall = time.perf_counter() - t0
+    per_order = {}
+    for r in res:
+        for k, v in r["per_order"].items():
+            per_order[k] = per_order.get(k, 0) + v
+    return {"tuples": sum(r["tuples"] for r in res), "seconds": max(r["seconds"] for r in res),
+            "per_order": per_order, "processes": nproc, "wall": wall}
 
 
-def cpu_baseline_entry(res):
-    return {"value": res["tuples"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{res['tuples']} tuples of the same workload, seeded and stratified by order "
-                       f"({res['per_order']}), {res['seconds']:.1f} s, one thread")}
+def cpu_baseline_entry(res, one=None):
+    cores = res.get("processes", 1)
+    out = {"value": res["tuples"] / res["seconds"], "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": (f"{res['tuples']} tuples of the same workload, seeded and stratified by order "
+                      f"({res['per_order']}), {res['seconds']:.1f} s, {cores} single-threaded process(es), "
+                      "one per host core")}
+    if one is not None:
+        out["one_core"] = {"value": one["tuples"] / one["seconds"], "unit": UNIT,
+                           "sample": f"{one['tuples']} tuples, {one['seconds']:.1f} s, one process"}
+    return out
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -394,7 +428,8 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline_entry(run_oracle_subprocess(args.cpu_seconds))
+        one = run_oracle_subprocess(args.cpu_seconds / 2, 1)
+        result["cpu_baseline"] = cpu_baseline_entry(run_oracle_subprocess(args.cpu_seconds, host_cores()), one)
     if rank == 0:
         print(json.dumps(result))
     ctx.close()
@@ -411,24 +446,26 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    cores = host_cores()
     for _ in range(args.warmup):
-        run_oracle_subprocess(args.ref_step_seconds / 4)
+        run_oracle_subprocess(args.ref_step_seconds / 4, cores)
     done = secs = 0.0
     per = []
     for _ in range(args.steps):
-        r = run_oracle_subprocess(args.ref_step_seconds)
+        r = run_oracle_subprocess(args.ref_step_seconds, cores)
         done += r["tuples"]
         secs += r["seconds"]
         per.append(r)
     value = done / secs
-    res = {"tuples": int(done), "seconds": secs, "per_order": per[-1]["per_order"]}
+    res = {"tuples": int(done), "seconds": secs, "per_order": per[-1]["per_order"], "processes": cores}
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
            "config": {"workload": WORKLOAD_DESC, "orders": "1-6",
                       "sample": f"each step: about {args.ref_step_seconds:.0f} s of oracle tuple CASCIs "
-                                "from a seeded, order-stratified sample"},
+                                f"from a seeded, order-stratified sample, in {cores} single-threaded "
+                                "processes (one per host core)"},
            "cpu_baseline": cpu_baseline_entry(res),
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -739,6 +776,8 @@ def main():
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-shard", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-shards", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--ncu-case", choices=["fp64", "mixed"], default=None,
                     help="run only casci_batch on one order of the workload (for ncu captures)")
     ap.add_argument("--ncu-order", type=int, default=6)
@@ -781,7 +820,7 @@ def main():
         run_screened(args)
         return
     if args.oracle_sample is not None:
-        print(json.dumps(oracle_sample(args.oracle_sample)))
+        print(json.dumps(oracle_sample(args.oracle_sample, shard=args.oracle_shard, nshards=args.oracle_shards)))
         return
     if args.ncu_case is not None:
         run_ncu_case(args)

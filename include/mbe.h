@@ -276,11 +276,22 @@ int casci_sigma_noalloc(int device, void *cuda_stream, int norb, const double *h
  *   n_tuples [n_orders], tuples [n_orders]  host arrays (tuples: device pointers to
  *                                           lexicographic order-m lists, m = 1..n_orders)
  *   exp_orbs [n_exp]                        host, the expansion space
- *   weights [n_orders]                      host array of device pointers, out
+ *   scale                                   every output is multiplied by scale (1 for
+ *                                           dE_MBE/dE_CAS itself; the upstream derivative
+ *                                           of a scalar loss otherwise)
+ *   weights [n_orders]                      host array of device pointers, out:
+ *                                           scale * w(S)
+ *   ref_weight [1]                          device out, or NULL: scale * w(R), the weight
+ *                                           of the reference-space CASCI, w(R) = 1 -
+ *                                           sum_S w(S) over every computed tuple (E_CAS(R)
+ *                                           enters the total directly and, through every
+ *                                           eps(S), with -w(S)); a fixed-order device
+ *                                           reduction
  * Errors: MBE_EINVAL, MBE_ECUDA.
  */
 int mbe_weights(mbe_ctx *ctx, int n_orders, const int64_t *n_tuples, const int32_t *const *tuples,
-                int n_exp, const int32_t *exp_orbs, double *const *weights);
+                int n_exp, const int32_t *exp_orbs, double scale, double *const *weights,
+                double *ref_weight);
 
 /*
  * Weighted Hellmann-Feynman gradients of tuple CASCI energies (the adjoint of

@@ -99,7 +99,7 @@ def lib() -> ctypes.CDLL:
     L.mbe_total.restype = i32
     L.mbe_total.argtypes = [P, i32, P, P, P, dbl, P, P]
     L.mbe_weights.restype = i32
-    L.mbe_weights.argtypes = [P, i32, P, P, i32, P, P]
+    L.mbe_weights.argtypes = [P, i32, P, P, i32, P, dbl, P, P]
     L.casci_rdm_batch.restype = i32
     L.casci_rdm_batch.argtypes = [P, i32, P, P, P, i32, P, i32, i64, P, ctypes.POINTER(MbeOpts), P, P, P, P]
     L.mbe_phi_gradient.restype = i32
@@ -354,17 +354,21 @@ class Context:
                                self._p(e_order), self._p(e_total)), "mbe_total")
         return e_order[:n], e_total
 
-    def mbe_weights(self, tuples: List[torch.Tensor], exp: Sequence[int]) -> List[torch.Tensor]:
-        """Adjoint weights w(S) of every tuple of orders 1..len(tuples)."""
+    def mbe_weights(self, tuples: List[torch.Tensor], exp: Sequence[int], scale: float = 1.0):
+        """Adjoint weights scale * w(S) of every tuple of orders 1..len(tuples), and
+        scale * w(R), w(R) = 1 - sum_S w(S), of the reference-space CASCI (a device
+        tensor of one element), all computed by the library."""
         n = len(tuples)
         out = [self._empty((t.shape[0],), torch.float64) for t in tuples]
+        ref_w = self._empty((1,), torch.float64)
         counts = (ctypes.c_int64 * max(n, 1))(*[int(t.shape[0]) for t in tuples])
         tp = (ctypes.c_void_p * max(n, 1))(*[self._p(t) for t in tuples])
         wp = (ctypes.c_void_p * max(n, 1))(*[self._p(t) for t in out])
         for t in tuples:
             self._dev(t, torch.int32, "tuples")
-        _check(lib().mbe_weights(self._h, n, counts, tp, len(exp), _i32_host(exp), wp), "mbe_weights")
-        return out
+        _check(lib().mbe_weights(self._h, n, counts, tp, len(exp), _i32_host(exp), float(scale), wp,
+                                 self._p(ref_w)), "mbe_weights")
+        return out, ref_w
 
     def casci_rdm_batch(self, h1, eri, occ, ref: Sequence[int], order: int, tuples: Optional[torch.Tensor],
                         weights: Optional[torch.Tensor], grad_h1: torch.Tensor,
@@ -431,7 +435,7 @@ class Context:
 
 def mbe_gradient(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequence[int], orders: Sequence[int],
                  skip: bool, opts: Optional[Opts] = None, two_body: bool = True, forward=None,
-                 occ_host: Optional[Sequence[int]] = None):
+                 occ_host: Optional[Sequence[int]] = None, scale: float = 1.0):
     """Gradient of the MBE energy with respect to h1 and (pq|rs), on the device.
 
     E_MBE = E_CAS(R) + sum_S w(S) eps(S) with the adjoint weights of Eq. 2, so
@@ -439,7 +443,8 @@ def mbe_gradient(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequence[i
                     + sum_S w(S) (dE_CAS(R u S) - dE_Phi),
     every term a Hellmann-Feynman density-matrix contraction.  `forward` is the
     dict of a previous run_mbe (its tuple lists are reused); opts should carry a
-    tight residual tolerance (default here 1e-9).
+    tight residual tolerance (default here 1e-9).  `scale` multiplies the
+    gradient (the library folds it into the adjoint weights).
     Returns (grad_h1 [norb, norb], grad_eri [norb]*4 or None, forward dict).
     """
     opts = opts or Opts(tol=1e-9)
@@ -448,11 +453,9 @@ def mbe_gradient(ctx: Context, h1, eri, occ, ref: Sequence[int], exp: Sequence[i
     norb = h1.shape[0]
     gh = torch.zeros((norb, norb), dtype=torch.float64, device=ctx.device)
     ge = torch.zeros((norb,) * 4, dtype=torch.float64, device=ctx.device) if two_body else None
-    w = ctx.mbe_weights(forward["tuples"], exp)
-    ctx.mbe_phi_gradient(occ, 1.0, gh, ge)
+    w, r_w = ctx.mbe_weights(forward["tuples"], exp, scale)
+    ctx.mbe_phi_gradient(occ, scale, gh, ge)
     if len(ref) > 0:
-        wsum = float(sum(x.sum() for x in w if x.numel() > 0)) if w else 0.0
-        r_w = torch.tensor([1.0 - wsum], dtype=torch.float64, device=ctx.device)
         ctx.casci_rdm_batch(h1, eri, occ, ref, 0, None, r_w, gh, ge, opts)
     for n, tup, wt in zip(orders, forward["tuples"], w):
         if tup.shape[0] > 0:
@@ -474,9 +477,10 @@ class MBEEnergy(torch.autograd.Function):
     def backward(fctx, grad_out):
         h1, eri, occ = fctx.saved_tensors
         ctx, ref, exp, orders, skip, opts, two_body, out = fctx.cfg
-        gh, ge, _ = mbe_gradient(ctx, h1, eri, occ, ref, exp, orders, skip, opts, two_body, forward=out)
-        g = grad_out.reshape(())
-        return g * gh, (g * ge if ge is not None else None), None, None, None, None, None, None, None, None
+        # the upstream derivative of the scalar output, read back and handed to the library
+        gh, ge, _ = mbe_gradient(ctx, h1, eri, occ, ref, exp, orders, skip, opts, two_body, forward=out,
+                                 scale=float(grad_out.reshape(()).item()))
+        return gh, ge, None, None, None, None, None, None, None, None
 
 
 EXPANSION_TYPES = ("type1", "type2", "type3")

@@ -91,6 +91,7 @@ __global__ void k_phi_energy(int norb, const double *h1, const double *eri, cons
 // ------------------------------------------------------------------ adjoint weights
 
 struct WeightArgs {
+    double scale;  // every weight is multiplied by this (the adjoint's upstream factor)
     int order;  // order m of the tuples whose weights this launch computes
     int n_max;  // highest order present
     int M;
@@ -101,7 +102,7 @@ struct WeightArgs {
 };
 
 // One thread per order-m tuple S: w(S) = 1 - sum over computed proper supersets U
-// of S of w(U).  Supersets S u J, J a j-subset (j = 1 .. n_max - m) of the
+// of S of w(U), scaled: s w(S) = s - sum_U s w(U).  Supersets S u J, J a j-subset (j = 1 .. n_max - m) of the
 // expansion orbitals outside S, are visited in lexicographic order of J.
 __global__ void k_weights(WeightArgs a, double *w_out)
 {
@@ -137,7 +138,28 @@ __global__ void k_weights(WeightArgs a, double *w_out)
             for (int l = i + 1; l < j; ++l) idx[l] = idx[l - 1] + 1;
         }
     }
-    w_out[t] = 1.0 - acc;
+    w_out[t] = a.scale - acc;
+}
+
+// Weight of the reference-space CASCI in E_MBE = E_CAS(R) + sum_S w(S) eps(S): its
+// energy enters the total once directly and, through eps(S) = E_CAS(R u S) -
+// E_Phi - E_ref,corr, once more with the weight -sum_S w(S) of every computed
+// tuple, so w(R) = 1 - sum_S w(S).  One block; fixed-shape reduction (strided
+// partial sums over the lists in order, then a tree), so the result is
+// deterministic.  With scaled weights s w(S): s w(R) = s - sum_S s w(S).
+__global__ void __launch_bounds__(RED_THREADS) k_ref_weight(SumLists S, int n_orders, double scale, double *out)
+{
+    __shared__ double part[RED_THREADS];
+    double s = 0.0;
+    for (int m = 0; m < n_orders; ++m)
+        for (int64_t i = threadIdx.x; i < S.count[m]; i += RED_THREADS) s += S.incs[m][i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = RED_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = scale - part[0];
 }
 
 // scale * dE_Phi/dtheta, one thread per ordered pair (i, j) of orbitals
@@ -211,7 +233,7 @@ int mbe_increments(mbe_ctx *ctx, int order, int64_t n_tuples, const int32_t *tup
 }
 
 int mbe_weights(mbe_ctx *ctx, int n_orders, const int64_t *n_tuples, const int32_t *const *tuples, int n_exp,
-                const int32_t *exp_orbs, double *const *weights)
+                const int32_t *exp_orbs, double scale, double *const *weights, double *ref_weight)
 {
     MBE_CHECK(ctx && n_tuples && tuples && weights && (n_exp == 0 || exp_orbs), MBE_EINVAL,
               "mbe_weights: NULL argument");
@@ -224,6 +246,7 @@ int mbe_weights(mbe_ctx *ctx, int n_orders, const int64_t *n_tuples, const int32
     for (int i = 0; i < n_exp; ++i) a.exp[i] = ex[i];
     a.M = n_exp;
     a.n_max = n_orders;
+    a.scale = scale;
     for (int m = 0; m < n_orders; ++m) {
         MBE_CHECK(n_tuples[m] >= 0 && (n_tuples[m] == 0 || (tuples[m] && weights[m])), MBE_EINVAL,
                   "mbe_weights: bad list of order %d", m + 1);
@@ -237,6 +260,16 @@ int mbe_weights(mbe_ctx *ctx, int n_orders, const int64_t *n_tuples, const int32
         a.order = m;
         unsigned g = (unsigned)((a.count[m - 1] + 127) / 128);
         k_weights<<<g, 128, 0, ctx->stream>>>(a, weights[m - 1]);
+        MBE_CU(cudaGetLastError());
+        ++ctx->launches;
+    }
+    if (ref_weight) {
+        SumLists S;
+        for (int m = 0; m < MBE_MAX_ORDER; ++m) {
+            S.incs[m] = m < n_orders ? weights[m] : nullptr;
+            S.count[m] = m < n_orders ? n_tuples[m] : 0;
+        }
+        k_ref_weight<<<1, RED_THREADS, 0, ctx->stream>>>(S, n_orders, scale, ref_weight);
         MBE_CU(cudaGetLastError());
         ++ctx->launches;
     }

@@ -7,6 +7,8 @@ dE/d(pq|rs) symmetry orbits), and against the exact Hubbard homogeneity
 t dE/dt + U dE/dU = E and trace(gamma) = N.
 """
 
+import math
+
 import numpy as np
 import pytest
 
@@ -47,13 +49,16 @@ def test_weights_match_oracle(eng, ctx):
     h1, eri, occ, _ = hubbard_ring_momentum(8, 1.0, 2.0)
     orders = [1, 2, 3, 4, 5]
     out = eng.run_mbe(ctx, dev(h1), dev(eri), dev(occ), [], list(range(8)), orders, True)
-    w = ctx.mbe_weights(out["tuples"], list(range(8)))
+    w, ref_w = ctx.mbe_weights(out["tuples"], list(range(8)))
     tup = {n: [tuple(r) for r in out["tuples"][i].cpu().tolist()] for i, n in enumerate(orders)}
     wo = adjoint.adjoint_weights(tup)
     for i, n in enumerate(orders):
         got = w[i].cpu().numpy()
         want = np.array([wo[t] for t in tup[n]])
         assert np.abs(got - want).max(initial=0.0) <= 1e-12
+    # the reference-space weight is 1 - sum_S w(S) (the oracle's weights, summed exactly)
+    want_r = 1.0 - math.fsum(wo[t] for n in orders for t in tup[n])
+    assert abs(float(ref_w.item()) - want_r) <= 1e-9
     # sum_S w(S) eps(S) equals the sum of the increments
     lhs = sum(float((wi * e).sum()) for wi, e in zip(w, out["eps"]))
     rhs = float(out["e_order"].sum())

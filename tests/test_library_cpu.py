@@ -81,3 +81,41 @@ def test_oracle_is_not_imported_by_the_package():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.replace("no CPU", ""), f
+
+
+def test_binding_does_no_arithmetic_on_tensor_values():
+    """The Python binding only marshals: every step of the path, the adjoint's
+    reference-space weight and upstream scale included, runs in the library.
+    No tensor reduction or arithmetic method is called, no matrix product is
+    formed, and no value read back from the device enters an arithmetic
+    expression."""
+    import ast
+
+    path = os.path.join(ROOT, "paper_1910_03527_gb300", "binding.py")
+    tree = ast.parse(open(path).read())
+    tensor_ops = {"sum", "mean", "prod", "cumsum", "abs", "sqrt", "exp", "log", "matmul", "mm", "dot", "add",
+                  "sub", "mul", "div", "add_", "sub_", "mul_", "div_", "clamp", "norm", "einsum", "max",
+                  "min", "where", "neg", "pow", "square", "fsum"}
+    host_modules = {"math", "os", "sys", "functools", "ctypes"}
+    bad = []
+
+    def reads_device(node):
+        # float(x) / int(x) of a tensor, or x.item()
+        for sub in ast.walk(node):
+            if isinstance(sub, ast.Call) and isinstance(sub.func, ast.Attribute) and sub.func.attr in (
+                    "item", "tolist", "cpu"):
+                return True
+        return False
+
+    for node in ast.walk(tree):
+        if isinstance(node, ast.Call) and isinstance(node.func, ast.Attribute) and node.func.attr in tensor_ops:
+            base = node.func.value
+            if not (isinstance(base, ast.Name) and base.id in host_modules):
+                bad.append((node.lineno, ast.unparse(node)))
+        if isinstance(node, (ast.BinOp, ast.AugAssign)):
+            if isinstance(node.op, ast.MatMult):
+                bad.append((node.lineno, ast.unparse(node)))
+            parts = [node.left, node.right] if isinstance(node, ast.BinOp) else [node.target, node.value]
+            if any(reads_device(p) for p in parts):
+                bad.append((node.lineno, ast.unparse(node)))
+    assert not bad, bad
