@@ -55,6 +55,10 @@ extern "C" {
 #define MBE_STATUS_MAXITER 1   /* iteration cap reached; eps holds the last Ritz value */
 #define MBE_STATUS_NONFINITE 2 /* a NaN or Inf appeared; eps is NaN              */
 #define MBE_STATUS_BADINPUT 3  /* malformed tuple (index range, order, overlap with R) */
+#define MBE_STATUS_DEGENERATE 4 /* converged, and the lowest eigenvalues of the two spin-flip
+                                   sectors (the alpha-beta string exchange, P c = +c and
+                                   P c = -c) lie within 1e-8 E_h: eps is valid, the ground
+                                   state and its density matrices are not unique */
 
 /* Tuple-enumeration flags. */
 #define MBE_SKIP_NO_OCC_OR_VIRT 1 /* drop a tuple whose active space R u Omega has no
@@ -65,10 +69,15 @@ extern "C" {
 /* Precision modes of casci_batch. */
 #define MBE_PREC_FP64 0  /* every sigma and every Davidson step in float64             */
 #define MBE_PREC_MIXED 1 /* float32 sigma and Davidson until the residual reaches
-                            tol_switch, then at least fp64_final_iters float64
-                            Davidson iterations; the residual norm, Rayleigh quotient
-                            and subspace eigenproblem that decide convergence and give
-                            eps are float64                                          */
+                            tol_switch; then a float64 refinement: tuple solvers of up
+                            to 416 determinants form one float64 sigma of the float32
+                            Ritz vector x0 (the anchor: theta0 = Rayleigh quotient,
+                            r0 = H x0 - theta0 x0) and continue the Davidson in
+                            float32 on H - theta0 from x0 (at least fp64_final_iters
+                            iterations, re-anchoring if it stalls), so that the
+                            energy theta0 + mu keeps float64 accuracy; the other
+                            solvers run at least fp64_final_iters float64 Davidson
+                            iterations                                               */
 
 typedef struct mbe_ctx mbe_ctx;
 
@@ -77,7 +86,7 @@ typedef struct mbe_opts {
     double tol;           /* converged when ||H x - lambda x||_2 <= tol (x unit norm) */
     double tol_switch;    /* mixed mode: float32 phase ends at this residual         */
     int max_iter;         /* cap on Davidson iterations per phase                    */
-    int fp64_final_iters; /* mixed mode: minimum float64 iterations                  */
+    int fp64_final_iters; /* mixed mode: minimum refinement iterations (see above)   */
     int sectors;          /* MBE_SECTORS_BOTH: the lowest state of the determinant
                              space; MBE_SECTORS_EVEN: the lowest state that is even
                              under the exchange of the alpha and beta strings (the
@@ -88,8 +97,11 @@ typedef struct mbe_opts {
 #define MBE_SECTORS_BOTH 0
 #define MBE_SECTORS_EVEN 1
 
-/* Fills *opts with the defaults: FP64, tol 1e-6, tol_switch 1e-5, max_iter 2000,
-   fp64_final_iters 2, MBE_SECTORS_BOTH.  Host only, synchronous. */
+/* Fills *opts with the defaults: FP64, tol 1e-7, tol_switch 1e-5, max_iter 2000,
+   fp64_final_iters 2, MBE_SECTORS_BOTH.  Host only, synchronous.  The residual
+   tolerance 1e-7 keeps every tuple energy within ~1e-13 E_h of the exact lowest
+   eigenvalue (the error is about |r|^2 / gap), which the Eq. 2 sums need: the
+   Rayleigh-quotient errors of ~10^5 tuples all have the same sign. */
 void mbe_default_opts(mbe_opts *opts);
 
 /* ------------------------------------------------------------------ context */
@@ -129,6 +141,16 @@ typedef struct mbe_timing {
 } mbe_timing;
 int mbe_ctx_set_timing(mbe_ctx *ctx, int enable);
 int mbe_ctx_timings(mbe_ctx *ctx, int max, mbe_timing *out, int *count);
+
+/* Measurement helper, not part of the method: the fused multiply-add throughput
+   of the context's GPU, the denominator of the roofline fraction of the solver
+   kernels (which are bound by plain float64 / float32 arithmetic).  Runs one
+   warm-up and `reps` (1..1000) timed launches of a kernel in which every thread
+   of 4 x 256-thread blocks per SM advances 8 independent chains a <- a*b + c,
+   and returns the best rate in TFLOP/s (2 flops per FMA), CUDA events on the
+   context's stream.  kind: 0 = float64, 1 = float32.  Synchronous.
+   Errors: MBE_EINVAL, MBE_ENOMEM, MBE_ECUDA. */
+int mbe_fma_peak(mbe_ctx *ctx, int kind, int reps, double *tflops);
 
 /* ------------------------------------------------------------------ a1: tuples */
 
@@ -248,9 +270,10 @@ int casci_sigma(mbe_ctx *ctx, int norb, const double *h1, const double *eri, con
  *   exceed MBE_NOALLOC_SCRATCH_BYTES, are rejected with MBE_EUNSUPPORTED and a
  *   message saying so.  The caller still passes and owns inputs and outputs
  *   (device pointers, same layouts as casci_sigma).
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture.  Every call reuses the same array and
+ * Every call looks up the array's device address (cudaGetSymbolAddress, with the
+ * device current; the lookup allocates nothing), so a device reset that reloads
+ * the module leaves no stale address; the very first call on a device loads the
+ * module, so make it before any stream capture.  Every call reuses the same array and
  * leaves the last call's contents in it; each call fully rewrites what it reads,
  * so nothing carries over.  Calls whose work overlaps on the GPU (other streams,
  * other host threads) race on the array: serialise them.
@@ -336,9 +359,12 @@ int mbe_phi_gradient(mbe_ctx *ctx, int norb, const uint8_t *occ, double scale, d
  * and layouts as casci_sigma; the same-spin part uses a compressed (CSR) copy
  * of the one-spin Hamiltonian.
  *   precision   MBE_PREC_FP64: float64 arithmetic; MBE_PREC_MIXED: float32
- *               arithmetic on a float32 copy of c (result written as float64)
+ *               arithmetic on a float32 copy of c (result written as float64), the
+ *               opposite-spin product on the tensor cores (tcgen05, TF32 split into
+ *               hi + lo pairs, hi*hi + hi*lo + lo*hi accumulated in float32)
  *   c, sigma    device [N], N = C(n_cas, k)^2, k = |O n A|; diag device or NULL
- * Synchronous set-up (occupations read back), then asynchronous on the stream.
+ * Synchronous set-up (occupations read back), then asynchronous on the stream
+ * (MBE_PREC_MIXED: synchronous, to report a tensor-core wait that ran out).
  * Errors: MBE_EINVAL, MBE_EUNSUPPORTED (n_cas > 16), MBE_ENOMEM, MBE_ECUDA.
  */
 int casci_sigma_large(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,

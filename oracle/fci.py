@@ -19,13 +19,14 @@ from __future__ import annotations
 
 import ctypes
 import functools
+import math
 
 import numpy as np
 
 from . import build as _build
 
 DENSE_MAX = 1500
-SPARSE_MAX_ENTRIES = 30_000_000
+SPARSE_MAX_ENTRIES = 64_000_000
 
 
 @functools.lru_cache(maxsize=1)
@@ -153,6 +154,16 @@ def rdm12(n: int, na: int, nb: int, c: np.ndarray, two_body: bool = True):
     return g.reshape(n, n), (G.reshape(n, n, n, n) if two_body else None)
 
 
+def max_connections(n: int, na: int, nb: int) -> int:
+    """Most non-zero elements in one row of the (na, nb) Hamiltonian: the determinant
+    itself, its single replacements of either spin, and its same-spin and
+    opposite-spin double replacements.  Only sizes the choice of eigensolver."""
+    sa, sb = na * (n - na), nb * (n - nb)
+    daa = math.comb(na, 2) * math.comb(n - na, 2)
+    dbb = math.comb(nb, 2) * math.comb(n - nb, 2)
+    return 1 + sa + sb + daa + dbb + sa * sb
+
+
 def lowest_eigenpair(h: np.ndarray, eri: np.ndarray, na: int, nb: int, tol: float = 1e-13,
                      want_vector: bool = False):
     """Lowest eigenvalue (and optionally its eigenvector) of the CAS Hamiltonian."""
@@ -168,7 +179,7 @@ def lowest_eigenpair(h: np.ndarray, eri: np.ndarray, na: int, nb: int, tol: floa
         H = h_dense(h, eri, na, nb)
         w, v = scipy.linalg.eigh(H, subset_by_index=[0, 0])
         return (float(w[0]), v[:, 0]) if want_vector else float(w[0])
-    conn = 1 + 2 * n * n + 4 * n ** 4
+    conn = max_connections(n, na, nb)
     v0 = np.cos(np.arange(N) * 0.7311) + 0.1  # deterministic start vector
     if N * conn <= SPARSE_MAX_ENTRIES:
         rows, cols, vals = h_coo(h, eri, na, nb)

@@ -25,14 +25,14 @@ MBE_PREC_MIXED = 1
 MBE_SKIP_NO_OCC_OR_VIRT = 1
 MBE_MAX_CAS = 12
 MBE_MAX_LARGE_CAS = 16
-STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "NONFINITE", 3: "BADINPUT"}
+STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "NONFINITE", 3: "BADINPUT", 4: "DEGENERATE"}
 
 EXPORTS = ("mbe_default_opts", "mbe_ctx_create", "mbe_ctx_set_stream", "mbe_ctx_destroy",
            "mbe_last_error", "mbe_ctx_sync", "mbe_ctx_launches", "mbe_ctx_set_timing",
            "mbe_ctx_timings", "mbe_tuples", "mbe_string_table", "mbe_phi_energy",
            "casci_batch", "casci_sigma", "casci_sigma_noalloc", "mbe_increments", "mbe_total",
            "mbe_weights", "casci_rdm_batch", "mbe_phi_gradient", "casci_sigma_large", "casci_solve",
-           "mbe_screen", "casci_batch_routed")
+           "mbe_screen", "casci_batch_routed", "mbe_fma_peak")
 
 
 class MbeOpts(ctypes.Structure):
@@ -111,6 +111,8 @@ def lib() -> ctypes.CDLL:
     L.casci_batch_routed.restype = i32
     L.casci_batch_routed.argtypes = [P, i32, P, P, P, i32, P, dbl, i32, i64, P, ctypes.POINTER(MbeOpts), i64,
                                      P, P, P]
+    L.mbe_fma_peak.restype = i32
+    L.mbe_fma_peak.argtypes = [P, i32, i32, ctypes.POINTER(dbl)]
     L.mbe_screen.restype = i32
     L.mbe_screen.argtypes = [P, i32, P, i32, P, i32, P, i32, i64, P, P, dbl, i32, dbl, i32, i64,
                              ctypes.POINTER(i64), P]
@@ -137,7 +139,7 @@ class Opts:
     """Davidson options of casci_batch (see mbe_opts in include/mbe.h)."""
 
     precision: str = "fp64"  # "fp64" or "mixed"
-    tol: float = 1e-6
+    tol: float = 1e-7
     tol_switch: float = 1e-5
     max_iter: int = 2000
     fp64_final_iters: int = 2
@@ -201,6 +203,13 @@ class Context:
         _check(lib().mbe_ctx_timings(self._h, max_records, buf, ctypes.byref(cnt)), "mbe_ctx_timings")
         return [(buf[i].order, buf[i].solver, buf[i].dpl, buf[i].ms) for i in range(min(cnt.value,
                                                                                        max_records))]
+
+    def fma_peak(self, kind: str, reps: int = 5) -> float:
+        """Measured fused multiply-add throughput (TFLOP/s) of the float64 or float32 pipe."""
+        out = ctypes.c_double()
+        _check(lib().mbe_fma_peak(self._h, {"fp64": 0, "fp32": 1}[kind], int(reps), ctypes.byref(out)),
+               "mbe_fma_peak")
+        return out.value
 
     # ---------------------------------------------------------------- helpers
     def _dev(self, t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:

@@ -26,7 +26,6 @@
 // persistent kernels that pull tuples from an atomic counter per bucket.
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -69,11 +68,9 @@ struct BatchArgs {
     int32_t *iters;
     char *scratch;
     size_t slot_bytes;
-    // mixed mode of the warp solver split in two launches: the float32 phase leaves
-    // each tuple's start vectors (xs, float [2 * WARP_MAX_NDET] per tuple) and its
-    // state (pstate: [flag, float32 sigma count] per tuple) for the float64 phase
+    // mixed mode of the warp solver: the mixed launch leaves each tuple's state
+    // (pstate: [flag, float32 sigma count] per tuple) for the float64 redo launch
     unsigned long long *counters2;
-    float *xs;
     int32_t *pstate;
     // adjoint (casci_rdm_batch): 0 = energies only, 1 = + 1-RDM, 2 = + 1- and 2-RDM
     int rdm;
@@ -140,6 +137,7 @@ struct Problem {
     double *Hs64;         // [Ns*HSS]
     float *Hs32;          // [Ns*HSS]
     double *diag;         // [N]
+    const float *diag32;  // [N] float32 copy of the diagonal (mixed warp solver), or NULL
     void *c;              // [N] vector sigma reads (T)
     void *sbuf;           // [N] sigma output staging (warp solver)
     int sector;           // spin-flip sector of the solver's vectors (+1 or -1)
@@ -284,21 +282,22 @@ __device__ inline double flip_if(double v, int neg)
 }
 __device__ inline float flip_if(float v, int neg) { return __int_as_float(__float_as_int(v) ^ (neg << 31)); }
 
-// a5: one element of sigma = H c.
-template <typename T>
+// a5: one element of sigma = H c, accumulated in T; the vector c may be stored
+// in a narrower type TV (the float64 sigma of a float32 anchor vector).
+template <typename T, typename TV = T>
 __device__ inline T sigma_elem(const Problem &pb, const T *__restrict__ V, const T *__restrict__ Hs,
-                               const T *__restrict__ c, int d)
+                               const TV *__restrict__ c, int d)
 {
     const int Ns = pb.Ns;
     int ia = d / Ns, ib = d - ia * Ns;
     const T *ha = Hs + ia * pb.HSS;
     const T *hb = Hs + ib * pb.HSS;
-    const T *crow = c + ia * Ns;
+    const TV *crow = c + ia * Ns;
     // Two independent accumulators per sum keep two FMA chains in flight.
     T acc0 = 0, acc1 = 0;
     for (int J = 0; J < Ns; ++J) {
-        acc0 = fma(ha[J], c[J * Ns + ib], acc0);
-        acc1 = fma(hb[J], crow[J], acc1);
+        acc0 = fma(ha[J], (T)c[J * Ns + ib], acc0);
+        acc1 = fma(hb[J], (T)crow[J], acc1);
     }
     const int32_t *ta = pb.tab + ia * pb.RS;
     const int32_t *tb = pb.tab + ib * pb.RS;
@@ -306,17 +305,17 @@ __device__ inline T sigma_elem(const Problem &pb, const T *__restrict__ V, const
     for (int x = 0; x < R; ++x) {
         int ea = ta[x];
         const T *vrow = V + entry_pair(ea) * pb.P;
-        const T *cr = c + entry_J(ea) * Ns;
+        const TV *cr = c + entry_J(ea) * Ns;
         T s0 = 0, s1 = 0;
         int y = 0;
         for (; y + 1 < R; y += 2) {
             int e0 = tb[y], e1 = tb[y + 1];
-            s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), cr[entry_J(e0)], s0);
-            s1 = fma(flip_if(vrow[entry_pair(e1)], entry_neg(e1)), cr[entry_J(e1)], s1);
+            s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), (T)cr[entry_J(e0)], s0);
+            s1 = fma(flip_if(vrow[entry_pair(e1)], entry_neg(e1)), (T)cr[entry_J(e1)], s1);
         }
         if (y < R) {
             int e0 = tb[y];
-            s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), cr[entry_J(e0)], s0);
+            s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), (T)cr[entry_J(e0)], s0);
         }
         T s = s0 + s1;
         if (x & 1) acc1 += flip_if(s, entry_neg(ea)); else acc0 += flip_if(s, entry_neg(ea));
@@ -450,6 +449,7 @@ constexpr double GUESS_NOISE = 1e-4;
 struct PhaseOut {
     double lambda, rnorm;
     int nsig, status;
+    double dnorm;  // anchored refinements: |d| of the Ritz vector x0 + d
 };
 
 // ------------------------------------------------------------------ density matrices (adjoint)
@@ -563,20 +563,77 @@ __device__ void rdm_flush(const BatchArgs &a, const Problem &pb, const double *g
     if (!g2) return;
     for (int e = tid; e < n * n * n * n; e += nt) {
         const int s = e % n, r = (e / n) % n, q = (e / (n * n)) % n, p = e / (n * n * n);
-        double G = g2[e] - (q == r ? g1[p * n + s] : 0.0);
+        double Gv = g2[e] - (q == r ? g1[p * n + s] : 0.0);
         const bool op = a.occ[A[p]], oq = a.occ[A[q]], orr = a.occ[A[r]];
         double phi = 0.0;
         if (p == q && r == s && op && orr) phi += (p == r) ? 2.0 : 4.0;
         if (p == s && q == r && p != q && op && oq) phi -= 2.0;
-        const double v = 0.5 * w * (G - phi);
+        const double v = 0.5 * w * (Gv - phi);
         if (v != 0.0) atomicAdd(&a.grad_eri[eri_index(norb, A[p], A[q], A[r], A[s])], v);
     }
 }
 
 // ------------------------------------------------------------------ warp solver
 
-template <typename T, int DPL>
-__device__ inline void sigma_warp(const Problem &pb, const T *V, const T *Hs, const T *c, T *sbuf, T (&out)[DPL])
+// The tuples of the warp solver (<= 416 determinants, <= 8 orbitals) have at most
+// WARP_RMAX single-replacement entries per string (k (n - k + 1), largest at n = 8,
+// k = 7); the launch checks it.
+constexpr int WARP_RMAX = 14;
+
+// a5 for the warp solver: the element of sigma_elem with the beta list of I_b
+// decoded once into registers (pair index and column of c packed in one word,
+// signs in a bit mask), so that the gathers of one alpha entry are all
+// independent and in flight together (the loop over the list is unrolled to
+// WARP_RMAX with the tail predicated off).
+template <typename T>
+__device__ inline T sigma_elem_warp(const Problem &pb, const T *__restrict__ V, const T *__restrict__ Hs,
+                                    const T *__restrict__ c, int d)
+{
+    const int Ns = pb.Ns, P = pb.P, R = pb.R;
+    const int ia = d / Ns, ib = d - ia * Ns;
+    const T *ha = Hs + ia * pb.HSS;
+    const T *hb = Hs + ib * pb.HSS;
+    const T *crow = c + ia * Ns;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int J = 0;
+    for (; J + 1 < Ns; J += 2) {
+        a0 = fma(ha[J], c[J * Ns + ib], a0);
+        a1 = fma(hb[J], crow[J], a1);
+        a2 = fma(ha[J + 1], c[(J + 1) * Ns + ib], a2);
+        a3 = fma(hb[J + 1], crow[J + 1], a3);
+    }
+    if (J < Ns) {
+        a0 = fma(ha[J], c[J * Ns + ib], a0);
+        a1 = fma(hb[J], crow[J], a1);
+    }
+    const int32_t *tb = pb.tab + ib * pb.RS;
+    uint32_t bw[WARP_RMAX];  // (J_y << 16) | pair_y
+    uint32_t bn = 0;         // bit y: sign of entry y
+#pragma unroll
+    for (int y = 0; y < WARP_RMAX; ++y) {
+        const int e = y < R ? tb[y] : 0;
+        bw[y] = ((uint32_t)entry_J(e) << 16) | (uint32_t)entry_pair(e);
+        bn |= (uint32_t)entry_neg(e) << y;
+    }
+    const int32_t *ta = pb.tab + ia * pb.RS;
+#pragma unroll 1
+    for (int x = 0; x < R; ++x) {
+        const int ea = ta[x];
+        const T *vrow = V + entry_pair(ea) * P;
+        const T *cr = c + entry_J(ea) * Ns;
+        T s[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int y = 0; y < WARP_RMAX; ++y)
+            if (y < R)
+                s[y & 3] = fma(flip_if(vrow[bw[y] & 0xffffu], (bn >> y) & 1u), cr[bw[y] >> 16], s[y & 3]);
+        const T sx = (s[0] + s[1]) + (s[2] + s[3]);
+        if (x & 1) a1 += flip_if(sx, entry_neg(ea)); else a0 += flip_if(sx, entry_neg(ea));
+    }
+    return (a0 + a1) + (a2 + a3);
+}
+
+template <typename T, int DPL, typename TV = T>
+__device__ inline void sigma_warp(const Problem &pb, const T *V, const T *Hs, const TV *c, T *sbuf, T (&out)[DPL])
 {
     const int lane = threadIdx.x & 31, Ns = pb.Ns;
     // c lies in one spin-flip sector (P c = sector * c) and H commutes with P, so
@@ -590,7 +647,11 @@ __device__ inline void sigma_warp(const Problem &pb, const T *V, const T *Hs, co
 #pragma unroll 1
     for (int h = lane; h < nh; h += 32) {
         const int d = ia * Ns + ib, pd = ib * Ns + ia;
-        const T v = (pb.sector < 0 && ia == ib) ? (T)0 : sigma_elem<T>(pb, V, Hs, c, d);
+        T v;
+        if constexpr (sizeof(T) == sizeof(TV))
+            v = (pb.sector < 0 && ia == ib) ? (T)0 : sigma_elem_warp<T>(pb, V, Hs, c, d);
+        else
+            v = (pb.sector < 0 && ia == ib) ? (T)0 : sigma_elem<T, TV>(pb, V, Hs, c, d);
         sbuf[d] = v;
         if (pd != d) sbuf[pd] = pb.sector > 0 ? v : -v;
         tri_advance(ia, ib, 32, Ns);
@@ -610,42 +671,86 @@ __device__ inline float tiny_norm<float>() { return 1e-6f; }
 template <>
 __device__ inline double tiny_norm<double>() { return 1e-13; }
 
-// One Davidson phase in precision T.  x: start vector (any norm) in, Ritz vector out.
+// Anchor of a float32 refinement (mixed mode): a unit vector x0, exact in
+// float32, whose image under A = H - theta0 was formed once in float64:
+// theta0 = x0.Hx0 / x0.x0 and r0 = H x0 - theta0 x0, stored in float32 (r0 is
+// small, so float32 keeps it to about 1e-7 of its own size).  The refinement
+// iterates x = x0 + d on A; every quantity it forms (d, A d, r0, the Ritz value
+// mu of A) is small, so float32 rounding is relative to those small numbers and
+// lambda = theta0 + mu keeps float64 accuracy.  A d of a correction comes from a
+// float32 sigma minus shift * d; its rounding (about u32 |H| |d|) enters the
+// Ritz value only at second order in |d|, and the coupling x0.(A v) is always
+// formed as v.r0 (A symmetric), never from the float32 image.
+struct Anchor {
+    const float *x0, *r0;  // shared [N]
+    float shift, shift_lo; // theta0 = shift + shift_lo (the images A t = (H t - shift t) - shift_lo t
+                           // of the corrections see the same theta0 as r0 to float64 accuracy)
+    float x0x0;            // |x0|^2 (1 up to rounding)
+};
+
+// A refinement is accepted when its residual is below tol and its correction is
+// small: the float32 images of the corrections carry an error of about
+// u32 |H|, which enters the Ritz value as d^T E d, so |d| <= MIX_DMAX keeps it
+// below ~1e-13 E_h; a larger converged correction re-anchors at x0 + d.
+constexpr double MIX_DMAX = 3e-4;
+
+// One Davidson phase in precision T (locally optimal 3-vector form: current
+// Ritz vector x, previous direction p, preconditioned residual t).
+// Plain (an == NULL): x is the start vector (any norm) in, the unit Ritz vector
+// out, and the return value's lambda its Ritz value of H.
+// Anchored (T = float): x is the correction d (zero in), the iterate is x0 + d,
+// and lambda is the Ritz value mu of A = H - theta0; the formulas below are the
+// plain ones with x -> x0 + d and H x -> r0 + A d (x0 = r0 = 0 when plain).
 template <typename T, int DPL>
-__device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, int min_iter,
-                                  int max_iter, bool steer)
+__device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, int min_iter, int max_iter,
+                                  bool steer, const Anchor *an = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const T *V = sizeof(T) == 8 ? (const T *)pb.V64 : (const T *)pb.V32;
     const T *Hs = sizeof(T) == 8 ? (const T *)pb.Hs64 : (const T *)pb.Hs32;
     T *c = (T *)pb.c;
     T *sbuf = (T *)pb.sbuf;
+    const bool anch = sizeof(T) == 4 && an != nullptr;
+    const float *x0s = anch ? an->x0 : nullptr;
+    const float *r0s = anch ? an->r0 : nullptr;
+    const T shift = anch ? (T)an->shift : (T)0;
+    const T shift_lo = anch ? (T)an->shift_lo : (T)0;
+    const T x0x0 = anch ? (T)an->x0x0 : (T)0;
+    auto X0 = [&](int d) -> T { return anch ? (T)x0s[d] : (T)0; };
+    auto R0 = [&](int d) -> T { return anch ? (T)r0s[d] : (T)0; };
     T hx[DPL], p[DPL], hp[DPL], ht[DPL];
     PhaseOut o;
     o.nsig = 0;
     o.status = MBE_STATUS_OK;
+    o.dnorm = 0.0;
 
-    T s = 0;
+    T lam = 0;
+    if (!anch) {
+        T s = 0;
 #pragma unroll
-    for (int j = 0; j < DPL; ++j) s += x[j] * x[j];
-    s = warp_sum(s);
-    T inv = (T)1 / sqrt(s);
+        for (int j = 0; j < DPL; ++j) s += x[j] * x[j];
+        s = warp_sum(s);
+        T inv = (T)1 / sqrt(s);
 #pragma unroll
-    for (int j = 0; j < DPL; ++j) {
-        x[j] *= inv;
-        int d = lane + 32 * j;
-        if (d < pb.N) c[d] = x[j];
-        p[j] = 0;
-        hp[j] = 0;
+        for (int j = 0; j < DPL; ++j) {
+            x[j] *= inv;
+            int d = lane + 32 * j;
+            if (d < pb.N) c[d] = x[j];
+        }
+        __syncwarp();
+        sigma_warp<T, DPL>(pb, V, Hs, c, sbuf, hx);
+        ++o.nsig;
+        __syncwarp();
+        T xh = 0;
+#pragma unroll
+        for (int j = 0; j < DPL; ++j) xh += x[j] * hx[j];
+        lam = warp_sum(xh);
+    } else {
+#pragma unroll
+        for (int j = 0; j < DPL; ++j) x[j] = hx[j] = 0;  // x = x0: A x = r0, mu = x0.r0 = 0
     }
-    __syncwarp();
-    sigma_warp<T, DPL>(pb, V, Hs, c, sbuf, hx);
-    ++o.nsig;
-    __syncwarp();
-    T xh = 0;
 #pragma unroll
-    for (int j = 0; j < DPL; ++j) xh += x[j] * hx[j];
-    T lam = warp_sum(xh);
+    for (int j = 0; j < DPL; ++j) p[j] = hp[j] = 0;
     bool have_p = false;
     T best = (T)3e38;
     int stall = 0;
@@ -656,10 +761,11 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
         for (int j = 0; j < DPL; ++j) {
             int d = lane + 32 * j;
             if (d < pb.N) {
-                T r = hx[j] - lam * x[j];
+                T r = (R0(d) + hx[j]) - lam * (X0(d) + x[j]);
                 rr += r * r;
                 const int pd = flip_det(d, pb.Ns);
-                T den = (T)pb.diag[d < pd ? d : pd] - lam;
+                const int cd = d < pd ? d : pd;
+                T den = (pb.diag32 ? (T)pb.diag32[cd] : (T)pb.diag[cd]) - shift - lam;
                 if (fabs(den) < (T)1e-4) den = den >= (T)0 ? (T)1e-4 : (T)-1e-4;
                 c[d] = r / den;
             }
@@ -683,22 +789,44 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
             }
         }
         // orthonormalise t against x and p (two passes)
+        T t0n = 0;
+        if (anch) {
+#pragma unroll
+            for (int j = 0; j < DPL; ++j) {
+                int d = lane + 32 * j;
+                if (d < pb.N) t0n += c[d] * c[d];
+            }
+            t0n = sqrt(warp_sum(t0n));
+        }
+        T xx = 1;
+        if (anch) {
+            T s = 0;
+#pragma unroll
+            for (int j = 0; j < DPL; ++j) {
+                int d = lane + 32 * j;
+                if (d < pb.N) {
+                    const T xj = X0(d) + x[j];
+                    s += xj * xj;
+                }
+            }
+            xx = warp_sum(s);
+        }
         for (int pass = 0; pass < 2; ++pass) {
             T ax = 0, ap = 0;
 #pragma unroll
             for (int j = 0; j < DPL; ++j) {
                 int d = lane + 32 * j;
                 if (d < pb.N) {
-                    ax += x[j] * c[d];
+                    ax += (X0(d) + x[j]) * c[d];
                     ap += p[j] * c[d];
                 }
             }
-            ax = warp_sum(ax);
+            ax = warp_sum(ax) / xx;
             ap = warp_sum(ap);
 #pragma unroll
             for (int j = 0; j < DPL; ++j) {
                 int d = lane + 32 * j;
-                if (d < pb.N) c[d] -= ax * x[j] + ap * p[j];
+                if (d < pb.N) c[d] -= ax * (X0(d) + x[j]) + ap * p[j];
             }
         }
         T tt = 0;
@@ -708,7 +836,7 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
             if (d < pb.N) tt += c[d] * c[d];
         }
         T tn = sqrt(warp_sum(tt));
-        if (!(tn > tiny_norm<T>())) {
+        if (anch ? !(tn > (T)1e-4 * t0n) : !(tn > tiny_norm<T>())) {
             // The correction lies in span{x, p}: nothing left to add.
             if (!steer && rn > (T)tol) o.status = MBE_STATUS_MAXITER;
             break;
@@ -723,62 +851,83 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
         sigma_warp<T, DPL>(pb, V, Hs, c, sbuf, ht);
         ++o.nsig;
         __syncwarp();
+        // G = [x p t]^T A [x p t]; a coupling x.(A v) is formed as v.r0 + d.(A v)
         T g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0;
 #pragma unroll
         for (int j = 0; j < DPL; ++j) {
             int d = lane + 32 * j;
             T tj = (d < pb.N) ? c[d] : (T)0;
-            g00 += x[j] * hx[j];
-            g01 += x[j] * hp[j];
-            g02 += x[j] * ht[j];
+            if (anch) ht[j] = (ht[j] - shift * tj) - shift_lo * tj;
+            const T r0j = (d < pb.N) ? R0(d) : (T)0;
+            g00 += x[j] * ((T)2 * r0j + hx[j]);
+            g01 += p[j] * r0j + x[j] * hp[j];
+            g02 += tj * r0j + x[j] * ht[j];
             g11 += p[j] * hp[j];
             g12 += p[j] * ht[j];
             g22 += tj * ht[j];
         }
         T G[3][3];
-        G[0][0] = warp_sum(g00);
-        G[0][1] = G[1][0] = warp_sum(g01);
-        G[0][2] = G[2][0] = warp_sum(g02);
+        const T sx = anch ? (T)1 / sqrt(xx) : (T)1;  // x of unit norm in the basis
+        G[0][0] = warp_sum(g00) * sx * sx;
+        G[0][1] = G[1][0] = warp_sum(g01) * sx;
+        G[0][2] = G[2][0] = warp_sum(g02) * sx;
         G[1][1] = warp_sum(g11);
         G[1][2] = G[2][1] = warp_sum(g12);
         G[2][2] = warp_sum(g22);
         T y[3];
         eig3<T>(G, have_p, y);
+        y[0] *= sx;  // back to the coefficient of x itself
         T w2 = y[1] * y[1] + y[2] * y[2];
         T q0 = -w2 * y[0], q1 = y[1] - w2 * y[1], q2 = y[2] - w2 * y[2];
-        T zn = sqrt(q0 * q0 + q1 * q1 + q2 * q2);
-        bool np_ok = zn > tiny_norm<T>() * (T)1e-3;
+        T zn = sqrt(q0 * q0 * xx + q1 * q1 + q2 * q2);
+        bool np_ok = zn > (anch ? (T)1e-30 : tiny_norm<T>() * (T)1e-3);
         T zi = np_ok ? (T)1 / zn : (T)0;
         T y0 = y[0], y1 = y[1], y2 = y[2];
         q0 *= zi;
         q1 *= zi;
         q2 *= zi;
-        T xx = 0, xhx = 0;
+        // new x: plain y0 x + y1 p + y2 t, normalised; anchored scaled by 1/y0 so
+        // that the coefficient of x0 stays 1 (d <- d + (y1 p + y2 t) / y0)
+        T nxx = 0, nxh = 0, nxr = 0, nx0 = 0;
 #pragma unroll
         for (int j = 0; j < DPL; ++j) {
             int d = lane + 32 * j;
             T tj = (d < pb.N) ? c[d] : (T)0;
+            const T x0j = (d < pb.N) ? X0(d) : (T)0;
+            const T r0j = (d < pb.N) ? R0(d) : (T)0;
             T nx = y0 * x[j] + y1 * p[j] + y2 * tj;
             T nhx = y0 * hx[j] + y1 * hp[j] + y2 * ht[j];
-            T npv = q0 * x[j] + q1 * p[j] + q2 * tj;
-            T nhp = q0 * hx[j] + q1 * hp[j] + q2 * ht[j];
+            T npv = q0 * (x0j + x[j]) + q1 * p[j] + q2 * tj;
+            T nhp = q0 * (r0j + hx[j]) + q1 * hp[j] + q2 * ht[j];
             x[j] = nx;
             hx[j] = nhx;
             p[j] = npv;
             hp[j] = nhp;
-            xx += nx * nx;
-            xhx += nx * nhx;
+            nxx += nx * nx;
+            nxh += nx * nhx;
+            nxr += nx * r0j;
+            nx0 += nx * x0j;
         }
         have_p = np_ok;
-        xx = warp_sum(xx);
-        xhx = warp_sum(xhx);
-        T xi = (T)1 / sqrt(xx);
+        nxx = warp_sum(nxx);
+        nxh = warp_sum(nxh);
+        T sc;
+        if (anch) {
+            nxr = warp_sum(nxr);
+            nx0 = warp_sum(nx0);
+            sc = (T)1 / y0;
+            // mu = (x.Ax) / (x.x), x = x0 + sc nx, A x = r0 + sc A nx, x0.r0 = 0
+            lam = (sc * (T)2 * nxr + sc * sc * nxh) / (x0x0 + sc * (T)2 * nx0 + sc * sc * nxx);
+            o.dnorm = (double)(fabs(sc) * sqrt(nxx));
+        } else {
+            sc = (T)1 / sqrt(nxx);
+            lam = nxh / nxx;
+        }
 #pragma unroll
         for (int j = 0; j < DPL; ++j) {
-            x[j] *= xi;
-            hx[j] *= xi;
+            x[j] *= sc;
+            hx[j] *= sc;
         }
-        lam = xhx / xx;
         __syncwarp();
     }
     o.lambda = (double)lam;
@@ -844,10 +993,24 @@ __device__ inline double sector_guess(int d, int Ns, SectorGuess sg)
 // The second sector is first converged to the residual SECTOR_TOL only. Its
 // Ritz value theta then lies within the residual norm rn of an eigenvalue, so
 // when theta - rn exceeds the first sector's eigenvalue by more than a float32
-// rounding margin the sector cannot hold a lower state near theta, and it is
-// not refined further.
-constexpr double SECTOR_TOL = 1e-2;
+// rounding margin the sector holds no lower state near theta, and it is not
+// refined further.  This bounds only the eigenvalue nearest theta: a Davidson
+// that still sits near an excited state of the sector, its lowest state not yet
+// found, would pass the test too.  The residual is therefore taken far down
+// before the decision (1e-4 of a Hamiltonian of norm ~10-100): at 1e-2, the
+// decision discarded odd-sector ground states of the synthetic molecule that lie
+// 0.17 E_h below the even ones.
+constexpr double SECTOR_TOL = 1e-4;
 __host__ __device__ inline double sector_margin(double lam) { return 1e-5 * (1.0 + fabs(lam)); }
+
+// Reading C3: a tuple whose two spin-flip sectors both converge to lowest
+// eigenvalues within DEGEN_TOL of each other has a degenerate ground state; its
+// energy is valid, its state (and density matrices) is not unique.
+constexpr double DEGEN_TOL = 1e-8;
+__host__ __device__ inline int with_degeneracy(int status, bool degen)
+{
+    return (status == MBE_STATUS_OK && degen) ? MBE_STATUS_DEGENERATE : status;
+}
 __host__ __device__ inline bool sector_loses(double theta, double rn, double lam, double tol_conv)
 {
     const double m = sector_margin(lam);
@@ -863,15 +1026,13 @@ __device__ inline void store_result(const BatchArgs &a, int64_t t, double eps, i
     if (a.iters) a.iters[t] = (n64 << 16) | (n32 & 0xffff);
 }
 
-// Warp-solver modes: WM_ALL runs both precisions in one kernel (float64 mode, and
-// the adjoint); in mixed mode WM_F32 runs the float32 phases of both spin-flip
-// sectors and decides the second, and WM_F64 finishes in float64. Split, each
-// kernel holds one precision's Davidson, which keeps the code executed on an SM
-// within the instruction cache.
-enum { WM_ALL = 0, WM_F32 = 1, WM_F64 = 2 };
-// pstate flags: the second sector lost (0), needs float64 (1); the float32 phase
-// of the first sector was not finite: redo everything in float64 (3)
-enum { PS_ONE = 0, PS_TWO = 1, PS_REDO = 3 };
+// Warp-solver modes of k_casci_warp: WM_ALL solves in float64 (float64 mode, and
+// the adjoint); WM_F64 redoes in float64 the tuples that the mixed solver
+// (k_casci_warp_mixed) flagged PS_REDO and skips the others.
+enum { WM_ALL = 0, WM_F64 = 2 };
+// pstate flags written by the mixed solver: the tuple is done (0); redo it in
+// float64 (3): a float32 phase was not finite, or a refinement did not converge
+enum { PS_DONE = 0, PS_REDO = 3 };
 
 template <int DPL, int MODE>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
@@ -890,6 +1051,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
         pos = __shfl_sync(FULL, pos, 0);
         if ((int64_t)pos >= cnt) break;
         const int64_t t = a.perm[begin + (int64_t)pos];
+        if (MODE == WM_F64 && a.pstate[2 * t] != PS_REDO) continue;
         if (lane == 0) build_A(a, t, A);
         __syncwarp();
         int k = 0;
@@ -904,6 +1066,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
         pb.R = ci.r;
         pb.RS = odd_stride(ci.r > 0 ? ci.r : 1);
         pb.HSS = odd_stride(ci.ns);
+        pb.diag32 = nullptr;
         uint32_t *str = (uint32_t *)(ws + L.off_str);
         int32_t *tab = (int32_t *)(ws + L.off_tab);
         for (int i = lane; i < ci.ns; i += 32) str[i] = ci.strings[i];
@@ -934,7 +1097,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
         int iphi = string_rank(mphi);
         double ephi = pb.diag[iphi * pb.Ns + iphi];
         if (pb.N == 1) {
-            if (MODE != WM_F32 && lane == 0) store_result(a, t, pb.diag[0] - ephi - a.e_ref_corr, MBE_STATUS_OK, 0, 0);
+            if (lane == 0) store_result(a, t, pb.diag[0] - ephi - a.e_ref_corr, MBE_STATUS_OK, 0, 0);
             __syncwarp();
             continue;
         }
@@ -969,65 +1132,15 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
                 bj = oi;
             }
         }
-        float *xs_t = a.xs + (size_t)t * 2 * WARP_MAX_NDET;
-        if constexpr (MODE == WM_F32) {
-            // float32 phases: the first sector to tol_switch; the second one to
-            // SECTOR_TOL, then tol_switch, decided against the first's float32
-            // eigenvalue (whose rounding the sector margin covers)
-            int n32 = 0, flag = PS_ONE;
-            double lam32 = 0.0;
-            for (int sector = 0; sector < 2; ++sector) {
-                if (sector == 1 && (pb.Ns < 2 || a.even_only)) break;
-                const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
-                pb.sector = sg.sgn;
-                float x32[DPL];
-#pragma unroll
-                for (int j = 0; j < DPL; ++j) {
-                    const int d = lane + 32 * j;
-                    x32[j] = (d < pb.N) ? (float)sector_guess(d, pb.Ns, sg) : 0.f;
-                }
-                bool finite = true, lose = false;
-                for (int pass = 0; pass < 1 + sector; ++pass) {
-                    const double tl = (sector == 0 || pass == 1) ? a.tol_switch : SECTOR_TOL;
-                    PhaseOut o32 = davidson_warp<float, DPL>(pb, x32, tl, 0, a.max_iter, true);
-                    n32 += o32.nsig;
-                    finite = o32.status != MBE_STATUS_NONFINITE;
-                    if (sector == 0) lam32 = o32.lambda;
-                    if (sector == 1) lose = !finite || sector_loses(o32.lambda, o32.rnorm, lam32, a.tol_switch);
-                    if (lose || !finite) break;
-                }
-                if (sector == 0 && !finite) {
-                    flag = PS_REDO;
-                    break;
-                }
-                if (sector == 1) flag = lose ? PS_ONE : PS_TWO;
-                if (sector == 0 || !lose) {
-#pragma unroll
-                    for (int j = 0; j < DPL; ++j) {
-                        const int d = lane + 32 * j;
-                        if (d < pb.N) xs_t[sector * pb.N + d] = x32[j];
-                    }
-                }
-            }
-            if (lane == 0) {
-                a.pstate[2 * t] = flag;
-                a.pstate[2 * t + 1] = n32;
-            }
-            __syncwarp();
-            continue;
-        } else {
+        {
             double x64[DPL];
             double *x2 = (double *)(ws + L.off_x2);
             double lam = 0.0;
             int status = MBE_STATUS_OK, n64 = 0, n32 = 0;
-            int flag = PS_REDO;
-            if constexpr (MODE == WM_F64) {
-                flag = a.pstate[2 * t];
-                n32 = a.pstate[2 * t + 1];
-            }
+            bool degen = false;
+            if constexpr (MODE == WM_F64) n32 = a.pstate[2 * t + 1];  // the mixed solver's float32 work
             for (int sector = 0; sector < 2; ++sector) {
                 if (sector == 1 && (pb.Ns < 2 || status != MBE_STATUS_OK || a.even_only)) break;
-                if (MODE == WM_F64 && sector == 1 && flag == PS_ONE) break;
                 const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
                 if (sector == 1 && a.rdm) {
     #pragma unroll
@@ -1037,11 +1150,10 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
                     }
                 }
                 pb.sector = sg.sgn;
-                const bool from_xs = MODE == WM_F64 && flag != PS_REDO;
     #pragma unroll
                 for (int j = 0; j < DPL; ++j) {
                     const int d = lane + 32 * j;
-                    x64[j] = (d < pb.N) ? (from_xs ? (double)xs_t[sector * pb.N + d] : sector_guess(d, pb.Ns, sg)) : 0.0;
+                    x64[j] = (d < pb.N) ? sector_guess(d, pb.Ns, sg) : 0.0;
                 }
                 // the second sector is refined in float64 only if its float32
                 // eigenvalue may lie below the first sector's
@@ -1065,9 +1177,10 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
     #pragma unroll
                         for (int j = 0; j < DPL; ++j) x64[j] = (double)x32[j];
                 }
-                // float64: in float64 mode the second sector's first pass (to SECTOR_TOL)
-                // decides; one call site keeps the kernel within the instruction cache
-                const bool pure64 = !mixed || (MODE == WM_F64 && flag == PS_REDO);
+                // float64: in float64 mode (and for a redo) the second sector's first
+                // pass (to SECTOR_TOL) decides; one call site keeps the kernel within
+                // the instruction cache
+                const bool pure64 = !mixed || MODE == WM_F64;
                 for (int pass = (sector == 1 && pure64) ? 0 : 1; pass < 2 && !lose; ++pass) {
                     const bool first = pass == 0;
                     PhaseOut o64 = davidson_warp<double, DPL>(pb, x64, first ? SECTOR_TOL : a.tol,
@@ -1081,6 +1194,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
                         lam = o64.lambda;
                         status = o64.status;
                     } else {
+                        degen = o64.status == MBE_STATUS_OK && fabs(o64.lambda - lam) <= DEGEN_TOL;
                         lose = o64.status == MBE_STATUS_NONFINITE || !(o64.lambda < lam);
                         if (!lose) {
                             lam = o64.lambda;
@@ -1101,7 +1215,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
             if (lane == 0) {
                 double e = status == MBE_STATUS_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL)
                                                           : lam - ephi - a.e_ref_corr;
-                store_result(a, t, e, status, n64, n32);
+                store_result(a, t, e, with_degeneracy(status, degen), n64, n32);
             }
             __syncwarp();
             if (a.rdm) {
@@ -1123,6 +1237,437 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
     }
 }
 
+// ------------------------------------------------------------------ mixed warp solver
+//
+// Mixed precision in one launch.  Each spin-flip sector runs the float32
+// Davidson to tol_switch (the second sector is decided there, as in the
+// float64 solver), then an anchored refinement: one float64 sigma of the
+// float32 Ritz vector x0 gives theta0 and r0 = (H - theta0) x0, and the float32
+// Davidson continues on A = H - theta0 from x0 (struct Anchor) until the
+// residual of x0 + d reaches tol; lambda = theta0 + mu.  A refinement that
+// stalls short of tol re-anchors at x0 + d (up to MIX_ANCHORS anchors); a
+// tuple whose refinement still fails, or whose float32 phase is not finite, is
+// flagged PS_REDO and solved again in float64 by the WM_F64 launch.  The float64
+// data of the anchor sigma (V, Hs) are kept as packed lower triangles, so that
+// a warp's shared memory stays near that of a float32-only solver.
+
+constexpr int MIX_ANCHORS = 3;
+
+__host__ __device__ inline int tri_index(int a, int b)
+{
+    const int hi = a > b ? a : b, lo = a > b ? b : a;
+    return hi * (hi + 1) / 2 + lo;
+}
+
+// One element of the float64 sigma of the vector c, from the packed lower
+// triangles Vp (pair x pair) and Hsp (string x string).
+__device__ inline double sigma_elem_anchor(const Problem &pb, const double *__restrict__ Vp,
+                                           const double *__restrict__ Hsp, const double *__restrict__ c, int d)
+{
+    const int Ns = pb.Ns;
+    const int ia = d / Ns, ib = d - ia * Ns;
+    const double *crow = c + ia * Ns;
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int J = 0; J < Ns; ++J) {
+        acc0 = fma(Hsp[tri_index(ia, J)], c[J * Ns + ib], acc0);
+        acc1 = fma(Hsp[tri_index(ib, J)], crow[J], acc1);
+    }
+    const int32_t *ta = pb.tab + ia * pb.RS;
+    const int32_t *tb = pb.tab + ib * pb.RS;
+    for (int x = 0; x < pb.R; ++x) {
+        const int ea = ta[x], px = entry_pair(ea);
+        const double *cr = c + entry_J(ea) * Ns;
+        double s = 0.0;
+        for (int y = 0; y < pb.R; ++y) {
+            const int e = tb[y];
+            s = fma(flip_if(Vp[tri_index(px, entry_pair(e))], entry_neg(e)), cr[entry_J(e)], s);
+        }
+        if (x & 1) acc1 += flip_if(s, entry_neg(ea)); else acc0 += flip_if(s, entry_neg(ea));
+    }
+    return acc0 + acc1;
+}
+
+// The anchor sigma over the half space of the vector's sector (see sigma_warp).
+template <int DPL>
+__device__ inline void sigma_warp_anchor(const Problem &pb, const double *Vp, const double *Hsp, const double *c,
+                                         double *sbuf, double (&out)[DPL])
+{
+    const int lane = threadIdx.x & 31, Ns = pb.Ns;
+    const int nh = Ns * (Ns + 1) / 2;
+    int ia = 0, ib = 0;
+    tri_advance(ia, ib, lane, Ns);
+#pragma unroll 1
+    for (int h = lane; h < nh; h += 32) {
+        const int d = ia * Ns + ib, pd = ib * Ns + ia;
+        const double v = (pb.sector < 0 && ia == ib) ? 0.0 : sigma_elem_anchor(pb, Vp, Hsp, c, d);
+        sbuf[d] = v;
+        if (pd != d) sbuf[pd] = pb.sector > 0 ? v : -v;
+        tri_advance(ia, ib, 32, Ns);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < DPL; ++j) {
+        const int d = lane + 32 * j;
+        out[j] = (d < pb.N) ? sbuf[d] : 0.0;
+    }
+    __syncwarp();
+}
+
+// Shared memory of one warp of the mixed solver (n orbitals, ns strings, r list
+// entries, N = ns^2 determinants at most).
+struct MixLayout {
+    int off_A, off_pp, off_Vp, off_V32, off_Hsp, off_Hs32, off_diag, off_c, off_s, off_x0, off_r0, off_str, off_tab,
+        bytes;
+};
+
+__host__ __device__ inline MixLayout mix_layout(int n, int ns, int r, int N)
+{
+    MixLayout L;
+    const int P = n * (n + 1) / 2, HSS = odd_stride(ns), RS = odd_stride(r > 0 ? r : 1);
+    const int vec = al16(4 * N);
+    int o = 0;
+    L.off_A = o; o = al16(o + 4 * MBE_MAX_CAS);
+    L.off_pp = o; o = al16(o + 4 * P);
+    L.off_Vp = o; o = al16(o + 8 * (P * (P + 1) / 2));
+    L.off_V32 = o; o = al16(o + 4 * P * P);
+    L.off_Hsp = o; o = al16(o + 8 * (ns * (ns + 1) / 2));
+    L.off_Hs32 = o; o = al16(o + 4 * ns * HSS);
+    L.off_diag = o; o = al16(o + 4 * N);
+    // c and sbuf of the float32 Davidson, contiguous: the anchor sigma's float64
+    // staging; during set-up the full float64 Hs, then the float64 diagonal
+    L.off_c = o;
+    L.off_s = o + vec;
+    o += 2 * vec > 8 * N ? 2 * vec : al16(8 * N);
+    // x0 and r0 of an anchor; during set-up h_eff and h' (float64)
+    L.off_x0 = o;
+    L.off_r0 = o + vec;
+    const int su = al16(8 * n * n) + 8 * P;
+    o += al16(2 * vec > su ? 2 * vec : su);
+    L.off_str = o; o = al16(o + 4 * ns);
+    L.off_tab = o; o = al16(o + 4 * ns * RS);
+    L.bytes = o;
+    return L;
+}
+
+// a2 + a4 for the mixed solver (one warp): h_eff and h' in float64 (scratch in
+// the anchor region), V as a packed float64 triangle and a full float32 copy,
+// Hs accumulated in float64 in the vector region and kept as a packed float64
+// triangle and a float32 copy, and the diagonal in float64 (left in the vector
+// region for the start vectors and Phi_A) and float32 (the preconditioner).
+__device__ void setup_mix(const BatchArgs &a, Problem &pb, char *ws, const MixLayout &L, double *Vp, double *Hsp,
+                          double *diag64)
+{
+    const int lane = threadIdx.x & 31;
+    const int n = pb.n, P = pb.P, norb = a.norb, Ns = pb.Ns;
+    double *h = (double *)(ws + L.off_x0);
+    double *hp = h + al16(8 * n * n) / 8;
+    double *Hf = (double *)(ws + L.off_c);  // full float64 Hs [Ns][Ns]
+    short *pp = (short *)pb.pp;
+    for (int e = lane; e < P; e += 32) {
+        int p = 0;
+        while ((p + 1) * (p + 2) / 2 <= e) ++p;
+        pp[2 * e] = (short)p;
+        pp[2 * e + 1] = (short)(e - p * (p + 1) / 2);
+    }
+    for (int e = lane; e < n * n; e += 32) {
+        const int x = e / n, y = e - x * n;
+        const int gp = pb.A[x], gq = pb.A[y];
+        double v = a.F[gp * norb + gq];
+        for (int c = 0; c < n; ++c) {
+            const int gi = pb.A[c];
+            if (a.occ[gi])
+                v -= 2.0 * a.eri[eri_index(norb, gp, gq, gi, gi)] - a.eri[eri_index(norb, gp, gi, gi, gq)];
+        }
+        h[e] = v;
+    }
+    __syncwarp();
+    for (int e = lane; e < P * P; e += 32) {
+        const int x = e / P, y = e - x * P;
+        const int p = pp[2 * x], q = pp[2 * x + 1], r = pp[2 * y], s = pp[2 * y + 1];
+        const double v = a.eri[eri_index(norb, pb.A[p], pb.A[q], pb.A[r], pb.A[s])];
+        pb.V32[e] = (float)v;
+        if (x >= y) Vp[tri_index(x, y)] = v;
+    }
+    __syncwarp();
+    for (int e = lane; e < P; e += 32) {
+        const int p = pp[2 * e], q = pp[2 * e + 1];
+        double v = h[p * n + q];
+        for (int r = 0; r < n; ++r) v -= 0.5 * Vp[tri_index(pair_index(p, r), pair_index(r, q))];
+        hp[e] = v;
+    }
+    __syncwarp();
+    // Hs, one column J per lane (as in setup_problem)
+    for (int J = lane; J < Ns; J += 32) {
+        for (int I = 0; I < Ns; ++I) Hf[I * Ns + J] = 0.0;
+        const int32_t *tj = pb.tab + J * pb.RS;
+        for (int b = 0; b < pb.R; ++b) {
+            const int eb = tj[b];
+            const int K = entry_J(eb), rs = entry_pair(eb);
+            const double sb = entry_neg(eb) ? -1.0 : 1.0;
+            Hf[K * Ns + J] += sb * hp[rs];
+            const int32_t *tk = pb.tab + K * pb.RS;
+            for (int q = 0; q < pb.R; ++q) {
+                const int ea = tk[q];
+                const double sa = entry_neg(ea) ? -1.0 : 1.0;
+                Hf[entry_J(ea) * Ns + J] += 0.5 * sa * sb * Vp[tri_index(entry_pair(ea), rs)];
+            }
+        }
+    }
+    __syncwarp();
+    for (int e = lane; e < Ns * Ns; e += 32) {
+        const int I = e / Ns, J = e - I * Ns;
+        const double v = Hf[e];
+        pb.Hs32[I * pb.HSS + J] = (float)v;
+        if (I >= J) Hsp[tri_index(I, J)] = v;
+    }
+    __syncwarp();
+    float *d32 = (float *)pb.diag32;
+    for (int d = lane; d < pb.N; d += 32) {
+        const int ia = d / Ns, ib = d - ia * Ns;
+        double v = Hsp[tri_index(ia, ia)] + Hsp[tri_index(ib, ib)];
+        uint32_t sa = pb.str[ia];
+        while (sa) {
+            const int p = __ffs((int)sa) - 1;
+            sa &= sa - 1;
+            uint32_t sb = pb.str[ib];
+            while (sb) {
+                const int q = __ffs((int)sb) - 1;
+                sb &= sb - 1;
+                v += Vp[tri_index(pair_index(p, p), pair_index(q, q))];
+            }
+        }
+        diag64[d] = v;
+        d32[d] = (float)v;
+    }
+    __syncwarp();
+}
+
+template <int DPL>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 3)
+    k_casci_warp_mixed(BatchArgs a, int bucket, MixLayout L)
+{
+    extern __shared__ __align__(16) char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    char *ws = smem + (size_t)wib * L.bytes;
+    const int64_t begin = a.bucket_off[bucket];
+    const int64_t cnt = a.bucket_off[bucket + 1] - begin;
+    const int n = a.n, P = n * (n + 1) / 2;
+    int *A = (int *)(ws + L.off_A);
+    double *Vp = (double *)(ws + L.off_Vp);
+    double *Hsp = (double *)(ws + L.off_Hsp);
+    double *diag64 = (double *)(ws + L.off_c);
+    double *sb64 = (double *)(ws + L.off_c);
+    float *x0s = (float *)(ws + L.off_x0);
+    float *r0s = (float *)(ws + L.off_r0);
+    for (;;) {
+        unsigned long long pos = 0;
+        if (lane == 0) pos = atomicAdd(&a.counters[bucket], 1ULL);
+        pos = __shfl_sync(FULL, pos, 0);
+        if ((int64_t)pos >= cnt) break;
+        const int64_t t = a.perm[begin + (int64_t)pos];
+        if (lane == 0) build_A(a, t, A);
+        __syncwarp();
+        int k = 0;
+        for (int i = 0; i < n; ++i) k += a.occ[A[i]];
+        const ClassInfo ci = a.cls[k];
+        Problem pb;
+        pb.n = n;
+        pb.P = P;
+        pb.k = k;
+        pb.Ns = ci.ns;
+        pb.N = ci.ns * ci.ns;
+        pb.R = ci.r;
+        pb.RS = odd_stride(ci.r > 0 ? ci.r : 1);
+        pb.HSS = odd_stride(ci.ns);
+        uint32_t *str = (uint32_t *)(ws + L.off_str);
+        int32_t *tab = (int32_t *)(ws + L.off_tab);
+        for (int i = lane; i < ci.ns; i += 32) str[i] = ci.strings[i];
+        for (int i = lane; i < ci.ns * ci.r; i += 32) {
+            const int row = i / ci.r, col = i - row * ci.r;
+            tab[row * pb.RS + col] = ci.table[i];
+        }
+        pb.str = str;
+        pb.tab = tab;
+        pb.A = A;
+        pb.pp = (const short *)(ws + L.off_pp);
+        pb.h = nullptr;
+        pb.hp = nullptr;
+        pb.V64 = nullptr;
+        pb.V32 = (float *)(ws + L.off_V32);
+        pb.Hs64 = nullptr;
+        pb.Hs32 = (float *)(ws + L.off_Hs32);
+        pb.diag = nullptr;
+        pb.diag32 = (const float *)(ws + L.off_diag);
+        pb.c = (void *)(ws + L.off_c);
+        pb.sbuf = (void *)(ws + L.off_s);
+        __syncwarp();
+        setup_mix(a, pb, ws, L, Vp, Hsp, diag64);
+        uint32_t mphi = 0;
+        for (int i = 0; i < n; ++i)
+            if (a.occ[A[i]]) mphi |= 1u << i;
+        const int iphi = string_rank(mphi);
+        const double ephi = diag64[iphi * pb.Ns + iphi];
+        if (pb.N == 1) {
+            if (lane == 0) {
+                store_result(a, t, diag64[0] - ephi - a.e_ref_corr, MBE_STATUS_OK, 0, 0);
+                a.pstate[2 * t] = PS_DONE;
+            }
+            __syncwarp();
+            continue;
+        }
+        // start vectors: the lowest diagonal element (ties -> lowest index), and for
+        // the P = -1 sector the lowest one with Ia != Ib
+        double best = 1e300, best_o = 1e300;
+        int bi = 0x7fffffff, bj = 0x7fffffff;
+        for (int d = lane; d < pb.N; d += 32) {
+            const double v = diag64[d];
+            if (v < best || (v == best && d < bi)) {
+                best = v;
+                bi = d;
+            }
+            const int ia = d / pb.Ns;
+            if (ia != d - ia * pb.Ns && (v < best_o || (v == best_o && d < bj))) {
+                best_o = v;
+                bj = d;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double ov = __shfl_xor_sync(FULL, best, o);
+            int oi = __shfl_xor_sync(FULL, bi, o);
+            if (ov < best || (ov == best && oi < bi)) {
+                best = ov;
+                bi = oi;
+            }
+            ov = __shfl_xor_sync(FULL, best_o, o);
+            oi = __shfl_xor_sync(FULL, bj, o);
+            if (ov < best_o || (ov == best_o && oi < bj)) {
+                best_o = ov;
+                bj = oi;
+            }
+        }
+        __syncwarp();  // the float64 diagonal is dead from here: its region holds c and sbuf
+        int n32 = 0, n64 = 0;
+        bool redo = false, degen = false;
+        double lam = 0.0, lam32 = 0.0;
+        for (int sector = 0; sector < 2 && !redo; ++sector) {
+            if (sector == 1 && (pb.Ns < 2 || a.even_only)) break;
+            const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
+            pb.sector = sg.sgn;
+            float xv[DPL];
+#pragma unroll
+            for (int j = 0; j < DPL; ++j) {
+                const int d = lane + 32 * j;
+                xv[j] = (d < pb.N) ? (float)sector_guess(d, pb.Ns, sg) : 0.f;
+            }
+            // plain float32 passes (the first sector one to tol_switch; the second one
+            // to SECTOR_TOL, then tol_switch, decided against the first's float32
+            // eigenvalue), then anchored refinements; one call site of the Davidson
+            int passes = 0, anchors = 0;
+            bool lose = false, fail = false, done = false;
+            double th = 0.0, lam_s = 0.0;
+            Anchor an{x0s, r0s, 0.f, 0.f, 1.f};
+            for (;;) {
+                const bool anchored = anchors > 0;
+                const double tl = anchored ? a.tol : ((sector == 0 || passes == 1) ? a.tol_switch : SECTOR_TOL);
+                PhaseOut o = davidson_warp<float, DPL>(pb, xv, tl, anchored ? a.min_fp64 : 0, a.max_iter, true,
+                                                       anchored ? &an : nullptr);
+                n32 += o.nsig;
+                if (!anchored) {
+                    const bool finite = o.status != MBE_STATUS_NONFINITE;
+                    if (sector == 0) {
+                        lam32 = o.lambda;
+                        if (!finite) {
+                            fail = true;
+                            break;
+                        }
+                    } else {
+                        lose = !finite || sector_loses(o.lambda, o.rnorm, lam32, a.tol_switch);
+                        if (lose) break;
+                    }
+                    ++passes;
+                    if (sector == 1 && passes < 2) continue;
+                } else {
+                    lam_s = th + o.lambda;
+                    if (o.status == MBE_STATUS_NONFINITE) {
+                        fail = true;
+                        break;
+                    }
+                    if (o.rnorm <= a.tol && o.dnorm <= MIX_DMAX) {
+                        done = true;
+                        break;
+                    }
+                    if (anchors >= MIX_ANCHORS) {
+                        fail = true;
+                        break;
+                    }
+                    // stalled short of tol: re-anchor at x0 + d (rounded to float32)
+#pragma unroll
+                    for (int j = 0; j < DPL; ++j) {
+                        const int d = lane + 32 * j;
+                        xv[j] = (d < pb.N) ? x0s[d] + xv[j] : 0.f;
+                    }
+                    __syncwarp();
+                }
+                // anchor at xv: float64 sigma (the vector staged in float64 over the
+                // anchor region, the result in the vector region), theta0, then x0 and
+                // r0 = (H - theta0) x0 in float32 over the staged vector
+                double *x64 = (double *)(ws + L.off_x0);
+#pragma unroll
+                for (int j = 0; j < DPL; ++j) {
+                    const int d = lane + 32 * j;
+                    if (d < pb.N) x64[d] = (double)xv[j];
+                }
+                __syncwarp();
+                double s0[DPL];
+                sigma_warp_anchor<DPL>(pb, Vp, Hsp, x64, sb64, s0);
+                ++n64;
+                double xs = 0.0, xx = 0.0;
+#pragma unroll
+                for (int j = 0; j < DPL; ++j) {
+                    xs += (double)xv[j] * s0[j];
+                    xx += (double)xv[j] * (double)xv[j];
+                }
+                xs = warp_sum(xs);
+                xx = warp_sum(xx);
+                th = xs / xx;
+#pragma unroll
+                for (int j = 0; j < DPL; ++j) {
+                    const int d = lane + 32 * j;
+                    if (d < pb.N) {
+                        x0s[d] = xv[j];
+                        r0s[d] = (float)(s0[j] - th * (double)xv[j]);
+                    }
+                }
+                __syncwarp();
+                an.shift = (float)th;
+                an.shift_lo = (float)(th - (double)an.shift);
+                an.x0x0 = (float)xx;
+                ++anchors;
+            }
+            if (sector == 0) {
+                if (fail || !done) redo = true;
+                lam = lam_s;
+            } else if (!lose) {
+                if (fail || !done) redo = true;
+                degen = fabs(lam_s - lam) <= DEGEN_TOL;
+                if (lam_s < lam) lam = lam_s;
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            if (redo) {
+                a.pstate[2 * t] = PS_REDO;
+                a.pstate[2 * t + 1] = n32;
+            } else {
+                a.pstate[2 * t] = PS_DONE;
+                store_result(a, t, lam - ephi - a.e_ref_corr, with_degeneracy(MBE_STATUS_OK, degen), n64, n32);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------------ block solver
 
 constexpr int MMAX = 20;  // Davidson subspace of the block solver
@@ -1131,11 +1676,15 @@ constexpr int KRED = 24;  // values per block reduction (>= MMAX + 1)
 // phase (a window of 10 moved work into float32 on the 40-orbital molecule but took
 // longer: this solver's float32 sigma is not much cheaper than its float64 one)
 constexpr int BLOCK_STALL = 3;
+// anchored refinement of the block solver: iterations without a 10% residual drop
+// before it re-anchors, and the number of anchors before the float64 fallback
+constexpr int BLOCK_ANCHOR_STALL = 25;
+constexpr int BLOCK_ANCHORS = 8;
 
 // Per-block workspace slot: the Davidson basis V, its image W = H V, the Ritz
 // vector x and H x, a spare correction vector, the diagonal and Hs.
 struct SlotLayout {
-    size_t off_V, off_W, off_x, off_hx, off_t, off_diag, off_Hs64, off_Hs32, off_x2, vec, bytes;
+    size_t off_V, off_W, off_x, off_hx, off_t, off_diag, off_Hs64, off_Hs32, off_x2, off_x0, vec, bytes;
 };
 
 __host__ __device__ inline SlotLayout slot_layout(int ns, int N)
@@ -1154,6 +1703,7 @@ __host__ __device__ inline SlotLayout slot_layout(int ns, int N)
     L.off_Hs64 = o; o += ((size_t)ns * HSS * 8 + 255) & ~(size_t)255;
     L.off_Hs32 = o; o += ((size_t)ns * HSS * 4 + 255) & ~(size_t)255;
     L.off_x2 = o; o += vec;
+    L.off_x0 = o; o += vec;  // float64 anchor of the mixed refinement
     L.bytes = o;
     return L;
 }
@@ -1363,9 +1913,18 @@ __device__ inline void sigma_block(const Problem &pb, const T *Vi, const T *Hs, 
     __syncthreads();
 }
 
+// Plain: x is the start vector in, the unit Ritz vector out.  Anchored (T =
+// float, anch): V[0] = x0 and W[0] = r0 = (H - shift) x0 are given (see struct
+// Anchor), every other basis vector is a correction whose image is the float32
+// sigma minus shift times it, the Ritz value is that of H - shift, the coupling
+// of x0 to a vector v is formed as v.r0, a thick restart keeps x0 and the
+// corrections of the two lowest Ritz vectors, and x returns the correction d of
+// the Ritz vector x0 + d.  steer: iterations without a 10% residual drop that end
+// the phase (0: none).
 template <typename T>
 __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *x, T *hx, T *tx, char *smem,
-                                   const BlockSmem &S, double tol, int min_iter, int max_iter, bool steer)
+                                   const BlockSmem &S, double tol, int min_iter, int max_iter, int steer,
+                                   double shift = 0.0, bool anch = false)
 {
     const int tid = threadIdx.x, nt = blockDim.x, N = pb.N;
     const T *Vi = sizeof(T) == 8 ? (const T *)pb.V64 : (const T *)pb.V32;
@@ -1382,21 +1941,25 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
     PhaseOut o;
     o.nsig = 0;
     o.status = MBE_STATUS_OK;
+    o.dnorm = 0.0;
+    const T shT = (T)shift, shT_lo = (T)(shift - (double)shT);
     T v[KRED];
-    {
+    if (!anch) {
         v[0] = 0;
         for (int d = tid; d < N; d += nt) v[0] += x[d] * x[d];
         block_sum_n<T>(v, 1, red);
         T inv = (T)1 / sqrt(v[0]);
         for (int d = tid; d < N; d += nt) V[d] = x[d] * inv;
+        __syncthreads();
+        sigma_block<T>(pb, Vi, Hs, V, W);
+        ++o.nsig;
+        v[0] = 0;
+        for (int d = tid; d < N; d += nt) v[0] += V[d] * W[d];
+        block_sum_n<T>(v, 1, red);
+        if (tid == 0) G[0] = (double)v[0];
+    } else if (tid == 0) {
+        G[0] = 0.0;  // x0.r0 = 0: shift is x0's Rayleigh quotient
     }
-    __syncthreads();
-    sigma_block<T>(pb, Vi, Hs, V, W);
-    ++o.nsig;
-    v[0] = 0;
-    for (int d = tid; d < N; d += nt) v[0] += V[d] * W[d];
-    block_sum_n<T>(v, 1, red);
-    if (tid == 0) G[0] = (double)v[0];
     __syncthreads();
     int m = 1;
     double theta = 0.0;
@@ -1423,7 +1986,7 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
             T r = hs - th * xs;
             v[0] += r * r;
             const int pd = flip_det(d, pb.Ns);
-            T den = (T)pb.diag[d < pd ? d : pd] - th;
+            T den = (T)(pb.diag[d < pd ? d : pd] - shift) - th;
             if (fabs(den) < (T)1e-4) den = den >= (T)0 ? (T)1e-4 : (T)-1e-4;
             const T td = r / den;
             tdst[d] = td;
@@ -1445,11 +2008,83 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
             if (rn < (T)0.9 * best) {
                 best = rn;
                 stall = 0;
-            } else if (++stall >= BLOCK_STALL) {
+            } else if (++stall >= steer) {
                 break;
             }
         }
-        if (m == MMAX) {
+        if (m == MMAX && anch) {
+            // Thick restart that keeps the anchor: V[0] = x0, W[0] = r0 stay; V[1], V[2]
+            // become the corrections of the two lowest Ritz vectors (both orthogonal
+            // to x0), orthonormalised.
+            for (int d = tid; d < N; d += nt) {
+                T u1 = 0, w1 = 0, u2 = 0, w2 = 0;
+                for (int i = 1; i < MMAX; ++i) {
+                    const T vi = V[(size_t)i * ld + d], wi = W[(size_t)i * ld + d];
+                    u1 += (T)ys[i] * vi;
+                    w1 += (T)ys[i] * wi;
+                    u2 += (T)y2s[i] * vi;
+                    w2 += (T)y2s[i] * wi;
+                }
+                V[ld + d] = u1;
+                W[ld + d] = w1;
+                V[2 * ld + d] = u2;
+                W[2 * ld + d] = w2;
+            }
+            __syncthreads();
+            v[0] = 0;
+            for (int d = tid; d < N; d += nt) v[0] += V[ld + d] * V[ld + d];
+            block_sum_n<T>(v, 1, red);
+            const T i1 = (T)1 / sqrt(v[0]);
+            for (int d = tid; d < N; d += nt) {
+                V[ld + d] *= i1;
+                W[ld + d] *= i1;
+            }
+            __syncthreads();
+            for (int pass = 0; pass < 2; ++pass) {
+                v[0] = 0;
+                for (int d = tid; d < N; d += nt) v[0] += V[ld + d] * V[2 * ld + d];
+                block_sum_n<T>(v, 1, red);
+                for (int d = tid; d < N; d += nt) {
+                    V[2 * ld + d] -= v[0] * V[ld + d];
+                    W[2 * ld + d] -= v[0] * W[ld + d];
+                }
+            }
+            v[0] = 0;
+            for (int d = tid; d < N; d += nt) v[0] += V[2 * ld + d] * V[2 * ld + d];
+            block_sum_n<T>(v, 1, red);
+            int mnew = 2;
+            const T n2 = sqrt(v[0]);
+            if (n2 > (T)1e-3) {
+                const T i2 = (T)1 / n2;
+                for (int d = tid; d < N; d += nt) {
+                    V[2 * ld + d] *= i2;
+                    W[2 * ld + d] *= i2;
+                }
+                mnew = 3;
+            }
+            __syncthreads();
+            v[0] = v[1] = v[2] = v[3] = v[4] = 0;
+            for (int d = tid; d < N; d += nt) {
+                v[0] += W[d] * V[ld + d];  // x0.(A u1) as u1.r0
+                v[1] += V[ld + d] * W[ld + d];
+                if (mnew == 3) {
+                    v[2] += W[d] * V[2 * ld + d];
+                    v[3] += V[ld + d] * W[2 * ld + d];
+                    v[4] += V[2 * ld + d] * W[2 * ld + d];
+                }
+            }
+            block_sum_n<T>(v, 5, red);
+            if (tid == 0) {
+                G[1] = G[MMAX] = (double)v[0];
+                G[MMAX + 1] = (double)v[1];
+                if (mnew == 3) {
+                    G[2] = G[2 * MMAX] = (double)v[2];
+                    G[MMAX + 2] = G[2 * MMAX + 1] = (double)v[3];
+                    G[2 * MMAX + 2] = (double)v[4];
+                }
+            }
+            m = mnew;
+        } else if (m == MMAX) {
             // Thick restart on the two lowest Ritz vectors of the current basis
             // (orthogonal by construction, so W stays consistent with H V).
             for (int d = tid; d < N; d += nt) {
@@ -1545,15 +2180,33 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
         for (int i = 0; i < KRED; ++i) v[i] = 0;
         for (int d = tid; d < N; d += nt) {
             T wd = wv[d];
+            if (anch) {
+                wd = (wd - shT * tv[d]) - shT_lo * tv[d];
+                wv[d] = wd;
+            }
 #pragma unroll
             for (int i = 0; i < MMAX + 1; ++i)
-                if (i <= m) v[i] += V[(size_t)i * ld + d] * wd;
+                if (i <= m) v[i] += (anch && i == 0) ? W[d] * tv[d] : V[(size_t)i * ld + d] * wd;
         }
         block_sum_n<T>(v, m + 1, red);
         if (tid == 0)
             for (int i = 0; i <= m; ++i) G[i * MMAX + m] = G[m * MMAX + i] = (double)v[i];
         __syncthreads();
         ++m;
+    }
+    if (anch) {
+        // the correction d of the Ritz vector, scaled so that x0 keeps coefficient 1
+        const T inv0 = (T)(1.0 / ys[0]);
+        v[0] = 0;
+        for (int d = tid; d < N; d += nt) {
+            T u = 0;
+            for (int i = 1; i < MMAX; ++i)
+                if (i < m) u += (T)ys[i] * V[(size_t)i * ld + d];
+            x[d] = u * inv0;
+            v[0] += x[d] * x[d];
+        }
+        block_sum_n<T>(v, 1, red);
+        o.dnorm = (double)sqrt(v[0]);
     }
     o.lambda = theta;
     o.rnorm = (double)rn;
@@ -1678,6 +2331,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
         double *x2 = (double *)(slot + L.off_x2);
         double lam = 0.0;
         int status = MBE_STATUS_OK, n64 = 0, n32 = 0;
+        bool degen = false;
         for (int sector = 0; sector < 2; ++sector) {
             if (sector == 1 && (pb.Ns < 2 || status != MBE_STATUS_OK || a.even_only)) break;
             const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
@@ -1686,7 +2340,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
             pb.sector = sg.sgn;
             for (int d = threadIdx.x; d < pb.N; d += blockDim.x) x64[d] = sector_guess(d, pb.Ns, sg);
             __syncthreads();
-            bool lose = false;
+            bool lose = false, refined = false;
             if (mixed) {
                 float *x32 = (float *)(slot + L.off_x);
                 // narrow x in place (float view of the same region), bottom up
@@ -1703,44 +2357,94 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
                     const double tl = (sector == 0 || pass == 1) ? a.tol_switch : SECTOR_TOL;
                     o32 = davidson_block<float>(pb, (float *)(slot + L.off_V), (float *)(slot + L.off_W), L.vec / 4,
                                                 x32, (float *)(slot + L.off_hx), (float *)(slot + L.off_t), smem, S,
-                                                tl, 0, a.max_iter, true);
+                                                tl, 0, a.max_iter, BLOCK_STALL);
                     n32 += o32.nsig;
                     if (sector == 1)
                         lose = o32.status == MBE_STATUS_NONFINITE ||
                                sector_loses(o32.lambda, o32.rnorm, lam, a.tol_switch);
                     if (lose || o32.status == MBE_STATUS_NONFINITE) break;
                 }
-                // widen x back to float64 in place, top down
-                for (int base = ((pb.N - 1) / (int)blockDim.x) * (int)blockDim.x; base >= 0;
-                     base -= (int)blockDim.x) {
-                    int d = base + threadIdx.x;
-                    float v = (d < pb.N) ? x32[d] : 0.0f;
+                const bool finite = o32.status != MBE_STATUS_NONFINITE;
+                double *x0 = (double *)(slot + L.off_x0);
+                if (!lose && finite) {
+                    // Anchored refinement (struct Anchor): a float64 sigma of the float64
+                    // anchor x0, then the float32 Davidson on H - theta0 with x0 as its
+                    // first basis vector; x0 <- x0 + d after each pass, re-anchoring while
+                    // the residual stays above tol.
+                    for (int d = threadIdx.x; d < pb.N; d += blockDim.x) x0[d] = (double)x32[d];
                     __syncthreads();
-                    if (d < pb.N) x64[d] = (o32.status == MBE_STATUS_NONFINITE) ? 0.0 : (double)v;
+                    float *V0 = (float *)(slot + L.off_V), *W0 = (float *)(slot + L.off_W);
+                    double *s0 = (double *)(slot + L.off_hx);
+                    bool done = false, bad = false;
+                    double lam_s = 0.0;
+                    for (int anc = 0; anc < BLOCK_ANCHORS && !done && !bad; ++anc) {
+                        sigma_block<double>(pb, pb.V64, pb.Hs64, x0, s0);
+                        ++n64;
+                        double q[KRED];
+                        q[0] = q[1] = 0.0;
+                        for (int d = threadIdx.x; d < pb.N; d += blockDim.x) {
+                            q[0] += x0[d] * s0[d];
+                            q[1] += x0[d] * x0[d];
+                        }
+                        block_sum_n<double>(q, 2, red);
+                        const double th = q[0] / q[1], inv = 1.0 / sqrt(q[1]);
+                        for (int d = threadIdx.x; d < pb.N; d += blockDim.x) {
+                            V0[d] = (float)(x0[d] * inv);
+                            W0[d] = (float)((s0[d] - th * x0[d]) * inv);
+                        }
+                        __syncthreads();
+                        PhaseOut o = davidson_block<float>(pb, V0, W0, L.vec / 4, x32, (float *)(slot + L.off_hx),
+                                                           (float *)(slot + L.off_t), smem, S, a.tol, a.min_fp64,
+                                                           a.max_iter, BLOCK_ANCHOR_STALL, th, true);
+                        n32 += o.nsig;
+                        lam_s = th + o.lambda;
+                        bad = o.status == MBE_STATUS_NONFINITE;
+                        done = !bad && o.rnorm <= a.tol && o.dnorm <= MIX_DMAX;
+                        if (!bad)
+                            for (int d = threadIdx.x; d < pb.N; d += blockDim.x) x0[d] = x0[d] * inv + (double)x32[d];
+                        __syncthreads();
+                    }
+                    // the refined vector (or the start of the float64 fallback) as x64
+                    for (int d = threadIdx.x; d < pb.N; d += blockDim.x)
+                        x64[d] = bad ? sector_guess(d, pb.Ns, sg) : x0[d];
                     __syncthreads();
-                }
-                if (o32.status == MBE_STATUS_NONFINITE) {
-                    for (int d = threadIdx.x; d < pb.N; d += blockDim.x) x64[d] = sector_guess(d, pb.Ns, sg);
+                    if (done) {
+                        refined = true;
+                        if (sector == 1) degen = status == MBE_STATUS_OK && fabs(lam_s - lam) <= DEGEN_TOL;
+                        if (sector == 0) {
+                            lam = lam_s;
+                            status = MBE_STATUS_OK;
+                        } else if (lam_s < lam) {
+                            lam = lam_s;
+                            status = MBE_STATUS_OK;
+                        } else {
+                            lose = true;
+                        }
+                    }
+                } else {
+                    for (int d = threadIdx.x; d < pb.N; d += blockDim.x)
+                        x64[d] = finite ? (double)x32[d] : sector_guess(d, pb.Ns, sg);
                     __syncthreads();
                 }
             } else if (sector == 1) {
                 PhaseOut o1 = davidson_block<double>(pb, (double *)(slot + L.off_V), (double *)(slot + L.off_W),
                                                      L.vec / 8, x64, (double *)(slot + L.off_hx),
                                                      (double *)(slot + L.off_t), smem, S, SECTOR_TOL, 0,
-                                                     a.max_iter, true);
+                                                     a.max_iter, BLOCK_STALL);
                 n64 += o1.nsig;
                 lose = o1.status == MBE_STATUS_NONFINITE || sector_loses(o1.lambda, o1.rnorm, lam, 0.0);
             }
-            if (!lose) {
+            if (!lose && !refined) {
                 PhaseOut o64 = davidson_block<double>(pb, (double *)(slot + L.off_V), (double *)(slot + L.off_W),
                                                       L.vec / 8, x64, (double *)(slot + L.off_hx),
                                                       (double *)(slot + L.off_t), smem, S, a.tol,
-                                                      mixed ? a.min_fp64 : 0, a.max_iter, false);
+                                                      mixed ? a.min_fp64 : 0, a.max_iter, 0);
                 n64 += o64.nsig;
                 if (sector == 0) {
                     lam = o64.lambda;
                     status = o64.status;
                 } else {
+                    degen = o64.status == MBE_STATUS_OK && status == MBE_STATUS_OK && fabs(o64.lambda - lam) <= DEGEN_TOL;
                     lose = o64.status == MBE_STATUS_NONFINITE || !(o64.lambda < lam);
                     if (!lose) {
                         lam = o64.lambda;
@@ -1757,7 +2461,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
         if (threadIdx.x == 0) {
             double e = status == MBE_STATUS_NONFINITE ? __longlong_as_double(0x7ff8000000000000LL)
                                                       : lam - ephi - a.e_ref_corr;
-            store_result(a, t, e, status, n64, n32);
+            store_result(a, t, e, with_degeneracy(status, degen), n64, n32);
         }
         __syncthreads();
         if (a.rdm) {
@@ -1871,6 +2575,23 @@ struct Bucket {
     int max_ns, max_r, max_n;
 };
 
+template <int DPL>
+static int launch_warp_mixed(mbe_ctx *ctx, const BatchArgs &a, int b, const MixLayout &L)
+{
+    const size_t smem = (size_t)L.bytes * WARPS_PER_BLOCK;
+    MBE_CHECK(smem <= ctx->smem_optin, MBE_EUNSUPPORTED, "casci_batch: mixed warp solver needs %zu B shared memory",
+              smem);
+    MBE_CU(cudaFuncSetAttribute(k_casci_warp_mixed<DPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_casci_warp_mixed<DPL>, WARPS_PER_BLOCK * 32,
+                                                         smem));
+    if (per_sm < 1) per_sm = 1;
+    k_casci_warp_mixed<DPL><<<ctx->sm_count * per_sm, WARPS_PER_BLOCK * 32, smem, ctx->stream>>>(a, b, L);
+    MBE_CU(cudaGetLastError());
+    ++ctx->launches;
+    return MBE_OK;
+}
+
 template <int DPL, int MODE>
 static int launch_warp_mode(mbe_ctx *ctx, const BatchArgs &a, int b, const WarpLayout &L, size_t smem)
 {
@@ -1885,8 +2606,8 @@ static int launch_warp_mode(mbe_ctx *ctx, const BatchArgs &a, int b, const WarpL
     return MBE_OK;
 }
 
-// One warp-solver bucket: in mixed mode (energies only) a float32 launch and a
-// float64 launch, timed as one.
+// One warp-solver bucket: in mixed mode (energies only) the mixed launch and the
+// float64 launch that redoes the tuples it flagged, timed as one.
 template <int DPL>
 static int launch_warp(mbe_ctx *ctx, const BatchArgs &a, int b, const Bucket &bk)
 {
@@ -1896,9 +2617,9 @@ static int launch_warp(mbe_ctx *ctx, const BatchArgs &a, int b, const Bucket &bk
               smem);
     TimedLaunch tl(ctx, a.order, 0, DPL);
     int rc;
-    if (a.xs != nullptr) {
-        const WarpLayout L32 = warp_layout(a.n, bk.max_ns, bk.max_r, bk.max_n, false, 4);
-        if ((rc = launch_warp_mode<DPL, WM_F32>(ctx, a, b, L32, (size_t)L32.bytes * WARPS_PER_BLOCK))) return rc;
+    if (a.pstate != nullptr) {
+        const MixLayout LM = mix_layout(a.n, bk.max_ns, bk.max_r, bk.max_n);
+        if ((rc = launch_warp_mixed<DPL>(ctx, a, b, LM))) return rc;
         if ((rc = launch_warp_mode<DPL, WM_F64>(ctx, a, b, L, smem))) return rc;
     } else {
         if ((rc = launch_warp_mode<DPL, WM_ALL>(ctx, a, b, L, smem))) return rc;
@@ -2000,7 +2721,7 @@ static int run_casci(mbe_ctx *ctx, int norb, const double *h1, const double *eri
         a.cls[k].r = st->r;
         int64_t N = st->ns * st->ns;
         int b;
-        if (n <= WARP_MAX_N && N <= WARP_MAX_NDET && rdm != 2) {
+        if (n <= WARP_MAX_N && N <= WARP_MAX_NDET && st->r <= WARP_RMAX && rdm != 2) {
             int di = 0;
             while (DPL_SET[di] * 32 < N) ++di;
             if (warp_bucket_of_dpl[di] < 0) {
@@ -2042,7 +2763,7 @@ static int run_casci(mbe_ctx *ctx, int norb, const double *h1, const double *eri
     size_t bytes = align256((size_t)norb * norb * 8) + align256((size_t)n_tuples * 4) * 2 +
                    5 * align256((MAX_BUCKETS + 1) * 8) + (size_t)block_grid_n * slot_bytes +
                    (own_out ? align256((size_t)n_tuples * 8) + align256((size_t)n_tuples * 4) : 0) + 1024;
-    if (split) bytes += align256((size_t)n_tuples * 2 * WARP_MAX_NDET * 4) + align256((size_t)n_tuples * 8);
+    if (split) bytes += align256((size_t)n_tuples * 8);
     void *ws = nullptr;
     int rc = workspace(ctx, bytes, &ws);
     if (rc) return rc;
@@ -2057,12 +2778,8 @@ static int run_casci(mbe_ctx *ctx, int norb, const double *h1, const double *eri
     int64_t *bucket_off = bump.take<int64_t>(MAX_BUCKETS + 1);
     char *scratch = nullptr;
     if (block_grid_n > 0) scratch = bump.take<char>((size_t)block_grid_n * slot_bytes);
-    a.xs = nullptr;
     a.pstate = nullptr;
-    if (split) {
-        a.xs = bump.take<float>((size_t)n_tuples * 2 * WARP_MAX_NDET);
-        a.pstate = bump.take<int32_t>((size_t)n_tuples * 2);
-    }
+    if (split) a.pstate = bump.take<int32_t>((size_t)n_tuples * 2);
     if (own_out) {
         a.eps = bump.take<double>((size_t)n_tuples);
         a.status = status_out ? status_out : bump.take<int32_t>((size_t)n_tuples);
@@ -2272,21 +2989,16 @@ __global__ void k_string_table(int n, int k, int64_t ns, int r, uint32_t *string
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MBE_NOALLOC_SCRATCH_BYTES];
 
-// Device address of g_noalloc_scratch per device, looked up once with that
-// device current.  In host code the symbol itself is only a host-side handle.
-static std::mutex g_noalloc_mutex;
-static void *g_noalloc_addr[MBE_MAX_DEVICES];
-
-static int noalloc_scratch(int device, void **out)
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// symbol itself is only a host-side handle.  The address is looked up on every
+// call (a lookup allocates nothing), so a device reset that reloads the module
+// cannot leave a stale address behind.
+static int noalloc_scratch(void **out)
 {
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
-        g_noalloc_addr[device] = p;
-    }
-    *out = g_noalloc_addr[device];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+    *out = p;
     return MBE_OK;
 }
 
@@ -2328,7 +3040,7 @@ extern "C" int casci_sigma_noalloc(int device, void *cuda_stream, int norb, cons
     MBE_CU(cudaGetDevice(&prev));
     if (prev != device) MBE_CU(cudaSetDevice(device));
     void *scratch = nullptr;
-    int rc = noalloc_scratch(device, &scratch);
+    int rc = noalloc_scratch(&scratch);
     if (rc == MBE_OK) {
         cudaStream_t st = (cudaStream_t)cuda_stream;
         Bump bump(scratch);
@@ -2393,6 +3105,8 @@ namespace mbe {
 
 constexpr int MLARGE = 12;      // Davidson basis of the large solver (<= MMAX)
 constexpr int LARGE_STALL = 20; // iterations without a 10% residual drop that end the sector-deciding pass
+constexpr int LARGE_ANCHORS = 8;         // anchored refinements before the float64 fallback
+constexpr int LARGE_ANCHOR_STALL = 30;   // iterations without a 10% drop before re-anchoring
 constexpr int LRED = MLARGE + 2;  // values per grid reduction
 constexpr int LARGE_THREADS = 256;
 constexpr int SIGMA_THREADS = 512;
@@ -2585,110 +3299,6 @@ __global__ void __launch_bounds__(SIGMA_THREADS) k_large_ab64(LargeCas L, const 
     }
 }
 
-// Opposite-spin part of sigma in float32, one CTA per alpha string Ia at a time
-// (written, not accumulated):
-//     T[p][Jb] = sum_{x in list(Ia)} A[x][p] c[J_x][Jb],    A[x][p] = s_x V[p_x][p],
-//     sigma[Ia][K] += s T[p][Jb]  for every (Jb, p) with inv[p][Jb] = (K, s),
-// where inv reads the beta lists backwards (E_pq|Jb> = s|K> iff E_qp|K> = s|Jb>;
-// each packed pair occurs at most once in a string's list). Warp w owns the
-// eight rows p = 8w..8w+7 of a T tile, lane l its columns 4l..4l+3; the tile of
-// c rows is prefetched into registers while the previous tile is multiplied.
-constexpr int AB_TJ = 128;  // columns of a T tile
-constexpr int AB_PF = 20;   // prefetched tile words per thread (host-checked)
-constexpr int AB_MAX_THREADS = 576;  // 4 x the padded pair count at 16 orbitals, rounded up
-
-__global__ void __launch_bounds__(AB_MAX_THREADS) k_large_ab32(LargeCas L, int Pp, int Nsp, const float *__restrict__ c,
-                                                    const int32_t *__restrict__ inv, double *__restrict__ sigma)
-{
-    extern __shared__ __align__(16) char smem[];
-    const int P = L.P, Ns = L.Ns, R = L.R;
-    const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    float *A = (float *)smem;                 // [R][Pp]
-    float *B = A + (size_t)R * Pp;            // [R][AB_TJ]
-    int *INV = (int *)(B + (size_t)R * AB_TJ);  // [Pp][AB_TJ], this tile's slice of inv
-    float *srow = (float *)(INV + (size_t)Pp * AB_TJ);  // [Ns]
-    int *Jx = (int *)(srow + Ns);             // [R]
-    const int p0 = 8 * w, j0 = 4 * lane;
-    const int nB = R * AB_TJ;
-    for (int Ia = blockIdx.x; Ia < Ns; Ia += gridDim.x) {
-        const int32_t *ta = L.tab + (size_t)Ia * R;
-        for (int i = tid; i < Ns; i += nt) srow[i] = 0.f;
-        for (int x = tid; x < R; x += nt) Jx[x] = entry_J(ta[x]);
-        for (int i = tid; i < R * Pp; i += nt) {
-            const int x = i / Pp, p = i - x * Pp;
-            const int e = ta[x];
-            A[i] = p < P ? flip_if(L.V32[entry_pair(e) * P + p], entry_neg(e)) : 0.f;
-        }
-        __syncthreads();
-        float pf[AB_PF];
-#pragma unroll
-        for (int k = 0; k < AB_PF; ++k) {
-            const int i = tid + k * nt;
-            const int x = i / AB_TJ, j = i - x * AB_TJ;
-            pf[k] = (i < nB && j < Ns) ? c[(size_t)Jx[x] * Ns + j] : 0.f;
-        }
-        for (int Jb0 = 0; Jb0 < Ns; Jb0 += AB_TJ) {
-#pragma unroll
-            for (int k = 0; k < AB_PF; ++k) {
-                const int i = tid + k * nt;
-                if (i < nB) B[i] = pf[k];
-            }
-            __syncthreads();
-            // this thread's slice of inv for the tile, copied asynchronously while it multiplies
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int p = p0 + i;
-                if (p < P) {
-                    const unsigned dst = (unsigned)__cvta_generic_to_shared(INV + p * AB_TJ + j0);
-                    const int32_t *src = inv + (size_t)p * Nsp + Jb0 + j0;
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
-                }
-            }
-            const int nxt = Jb0 + AB_TJ;
-            if (nxt < Ns) {
-#pragma unroll
-                for (int k = 0; k < AB_PF; ++k) {
-                    const int i = tid + k * nt;
-                    const int x = i / AB_TJ, j = nxt + (i - x * AB_TJ);
-                    pf[k] = (i < nB && j < Ns) ? c[(size_t)Jx[x] * Ns + j] : 0.f;
-                }
-            }
-            float acc[8][4];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-#pragma unroll 2
-            for (int x = 0; x < R; ++x) {
-                const float4 a0 = *(const float4 *)(A + (size_t)x * Pp + p0);
-                const float4 a1 = *(const float4 *)(A + (size_t)x * Pp + p0 + 4);
-                const float4 b = *(const float4 *)(B + (size_t)x * AB_TJ + j0);
-                const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                const float bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-            }
-            asm volatile("cp.async.wait_all;\n" ::: "memory");
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int p = p0 + i;
-                if (p < P) {
-                    const int4 e4 = *(const int4 *)(INV + p * AB_TJ + j0);
-                    const int ev[4] = {e4.x, e4.y, e4.z, e4.w};
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (ev[j] >= 0) atomicAdd(&srow[ev[j] >> 1], flip_if(acc[i][j], ev[j] & 1));
-                }
-            }
-            __syncthreads();
-        }
-        for (int K = tid; K < Ns; K += nt) sigma[(size_t)Ia * Ns + K] = (double)srow[K];
-        __syncthreads();
-    }
-}
-
 // Same-spin part, row-streamed: out[I][K] += sum_e val[e] X[col[e]][K] over the
 // CSR row I of Hs, for a block of SS_ROWS rows and a tile of SS_TK columns per
 // work item. Column tiles are the outer work index, so the CTAs in flight share
@@ -2761,16 +3371,11 @@ __global__ void k_large_transpose(const T *__restrict__ in, int Ns, T *__restric
     }
 }
 
-// tabT[y * Ns + J] = tab[J * R + y]; inv[p * Nsp + J] = (K << 1) | neg for the
-// entry (K, p, neg) of J's list (inv preset to -1).
-__global__ void k_large_tables(LargeCas L, int32_t *tabT, int Nsp, int32_t *inv)
+// tabT[y * Ns + J] = tab[J * R + y] (the beta lists of the float64 opposite-spin term)
+__global__ void k_large_tables(LargeCas L, int32_t *tabT)
 {
     for (int J = blockIdx.x * blockDim.x + threadIdx.x; J < L.Ns; J += gridDim.x * blockDim.x)
-        for (int y = 0; y < L.R; ++y) {
-            const int e = L.tab[(size_t)J * L.R + y];
-            tabT[(size_t)y * L.Ns + J] = e;
-            if (inv) inv[(size_t)entry_pair(e) * Nsp + J] = (entry_J(e) << 1) | entry_neg(e);
-        }
+        for (int y = 0; y < L.R; ++y) tabT[(size_t)y * L.Ns + J] = L.tab[(size_t)J * L.R + y];
 }
 
 // ---- grid-wide vector algebra of the large Davidson (all float64)
@@ -2820,7 +3425,7 @@ __global__ void k_multidot_final(const double *partial, int nblocks, int K, doub
 // |r|^2 and |t|^2 (two values per block).
 __global__ void __launch_bounds__(LARGE_THREADS) k_ritz(const double *V, const double *W, size_t ld, int m,
                                                         const double *ys, const double *misc, const double *diag,
-                                                        int64_t N, double *x, double *hx, double *t,
+                                                        double shift, int64_t N, double *x, double *hx, double *t,
                                                         double *partial)
 {
     __shared__ double red[64];
@@ -2840,7 +3445,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_ritz(const double *V, const d
         x[d] = xs;
         hx[d] = hs;
         double r = hs - th * xs;
-        double den = diag[d] - th;
+        double den = (diag[d] - shift) - th;
         if (fabs(den) < 1e-4) den = den >= 0.0 ? 1e-4 : -1e-4;
         double td = r / den;
         t[d] = td;
@@ -2997,14 +3602,11 @@ namespace mbe {
 
 struct LargePlan {
     LargeCas L;
-    int grid_ab64, grid_ab32, grid_ss64, grid_ss32, grid_vec, grid_tr;
-    size_t smem_ab64, smem_ab32, smem_ss64, smem_ss32;
-    int Pp, Nsp, ab32_threads;
-    int32_t *inv;  // float32 form only: beta lists read backwards [P][Nsp]
+    int grid_ab64, grid_ss64, grid_ss32, grid_vec, grid_tr;
+    size_t smem_ab64, smem_ss64, smem_ss32;
     void *cT;      // transposed coefficients (room for N float64)
 };
 
-static int64_t large_nsp(int64_t ns) { return (ns + AB_TJ - 1) / AB_TJ * AB_TJ; }
 
 // Sets up one large CAS; the dense Hs may live in `dense_at` (e.g. the Davidson
 // basis region, unused during set-up). `fp32` adds the float32 sigma's tables.
@@ -3057,9 +3659,6 @@ static int large_setup(mbe_ctx *ctx, int norb, const double *h1, const double *e
     int64_t *off = bump.take<int64_t>((size_t)L.Ns + 1);
     int32_t *tabT = bump.take<int32_t>((size_t)L.R * L.Ns);
     L.tabT = tabT;
-    plan->Pp = (P + 7) / 8 * 8;
-    plan->Nsp = (int)large_nsp(L.Ns);
-    plan->inv = fp32 ? bump.take<int32_t>((size_t)P * plan->Nsp) : nullptr;
     plan->cT = bump.take<double>((size_t)L.N);  // float32 or float64 use
     L.Hd = dense_at ? dense_at : bump.take<double>((size_t)L.Ns * L.Ns);
     // (all of the above fits: the caller sized the workspace with large_bytes)
@@ -3078,9 +3677,7 @@ static int large_setup(mbe_ctx *ctx, int norb, const double *h1, const double *e
     k_scan_counts<<<1, 256, 0, ctx->stream>>>(cnt, L.Ns, off);
     k_large_hs_fill<<<wgrid, 256, 0, ctx->stream>>>(L, off);
     k_large_diag<<<ctx->sm_count * 8, 256, 0, ctx->stream>>>(L);
-    if (plan->inv)
-        MBE_CU(cudaMemsetAsync(plan->inv, 0xff, (size_t)P * plan->Nsp * sizeof(int32_t), ctx->stream));
-    k_large_tables<<<(L.Ns + 255) / 256, 256, 0, ctx->stream>>>(L, tabT, plan->Nsp, plan->inv);
+    k_large_tables<<<(L.Ns + 255) / 256, 256, 0, ctx->stream>>>(L, tabT);
     MBE_CU(cudaGetLastError());
     ctx->launches += 8;
     *k_out = k;
@@ -3105,21 +3702,6 @@ static int large_setup(mbe_ctx *ctx, int norb, const double *h1, const double *e
     MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_large_ss<float, false>, SS_THREADS, plan->smem_ss32));
     plan->grid_ss32 = ctx->sm_count * (b > 0 ? b : 1);
     plan->grid_tr = ctx->sm_count * 8;
-    if (fp32) {
-        const int R = L.R, Pp = plan->Pp;
-        plan->ab32_threads = 4 * Pp;  // one warp per 8 rows of a T tile
-        MBE_CHECK(plan->ab32_threads <= AB_MAX_THREADS, MBE_EUNSUPPORTED, "large CASCI: %d pairs", P);
-        MBE_CHECK((int64_t)R * AB_TJ <= (int64_t)AB_PF * plan->ab32_threads, MBE_EUNSUPPORTED,
-                  "large CASCI: %d list entries exceed the float32 sigma's prefetch", R);
-        plan->smem_ab32 = (size_t)R * Pp * 4 + (size_t)R * AB_TJ * 4 + (size_t)Pp * AB_TJ * 4 + (size_t)L.Ns * 4 +
-                          (size_t)R * 4;
-        MBE_CHECK(plan->smem_ab32 <= ctx->smem_optin, MBE_EUNSUPPORTED,
-                  "large CASCI: float32 sigma needs %zu B shared memory", plan->smem_ab32);
-        MBE_CU(cudaFuncSetAttribute(k_large_ab32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)plan->smem_ab32));
-        MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_large_ab32, plan->ab32_threads, plan->smem_ab32));
-        plan->grid_ab32 = ctx->sm_count * (b > 0 ? b : 1);
-    }
     plan->grid_vec = ctx->sm_count * 4;
     return MBE_OK;
 }
@@ -3135,7 +3717,6 @@ static size_t large_bytes(int norb, int n, int k, bool dense_separate, bool fp32
                align256(ns * conn * 8) + align256(ns * conn * 4) + align256(N * 8) + align256(ns * 4) +
                align256((ns + 1) * 8) + 4096;
     b += align256((size_t)k * (n - k + 1) * ns * 4) + align256((size_t)N * 8);
-    if (fp32) b += align256((size_t)P * large_nsp(ns) * 4);
     if (dense_separate) b += align256((size_t)ns * ns * 8);
     return b;
 }
@@ -3151,8 +3732,10 @@ static int large_sigma_launch(mbe_ctx *ctx, const LargePlan &pl, const T *c, dou
     if (sizeof(T) == 8) {
         k_large_ab64<<<pl.grid_ab64, SIGMA_THREADS, pl.smem_ab64, ctx->stream>>>(pl.L, (const double *)c, sigma);
     } else {
-        k_large_ab32<<<pl.grid_ab32, pl.ab32_threads, pl.smem_ab32, ctx->stream>>>(pl.L, pl.Pp, pl.Nsp,
-                                                                                  (const float *)c, pl.inv, sigma);
+        // the dense product on the tensor cores (large_tc.cu)
+        const int rc = large_ab_tc(ctx->stream, ctx->sm_count, ctx->smem_optin, pl.L.P, pl.L.Ns, pl.L.R, pl.L.tab,
+                                   pl.L.V32, (const float *)c, sigma, ctx->dev_err);
+        if (rc) return rc;
     }
     const int grid_ss = sizeof(T) == 8 ? pl.grid_ss64 : pl.grid_ss32;
     const size_t smem_ss = sizeof(T) == 8 ? pl.smem_ss64 : pl.smem_ss32;
@@ -3200,7 +3783,9 @@ extern "C" int casci_sigma_large(mbe_ctx *ctx, int norb, const double *h1, const
     float *c32 = bump.take<float>((size_t)N);
     k_to_float<<<pl.grid_vec, 256, 0, ctx->stream>>>(c, N, c32);
     ++ctx->launches;
-    return large_sigma_launch<float>(ctx, pl, c32, sigma, n_cas);
+    rc = large_sigma_launch<float>(ctx, pl, c32, sigma, n_cas);
+    if (rc) return rc;
+    return check_dev_err(ctx);  // the tensor-core product reports a wait that ran out
 }
 
 namespace mbe {
@@ -3222,6 +3807,75 @@ __global__ void k_lincomb2(const double *V, const double *W, size_t ld, int m, c
             }
         x2[d] = xs;
         hx2[d] = hs;
+    }
+}
+
+// Projects v onto the spin-flip sector sgn (v[Ia][Ib] = sgn v[Ib][Ia]), pairs
+// (d, P d) averaged: the large solver's sigma is not formed over a half space,
+// so its rounding would otherwise let the other sector's lower states leak in.
+__global__ void k_project_sector(double *v, int Ns, int sgn, int64_t N)
+{
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < N; d += (int64_t)gridDim.x * blockDim.x) {
+        const int ia = (int)(d / Ns), ib = (int)(d - (int64_t)ia * Ns);
+        if (ia == ib) {
+            if (sgn < 0) v[d] = 0.0;
+        } else if (ia < ib) {
+            const int64_t pd = (int64_t)ib * Ns + ia;
+            const double m = 0.5 * (v[d] + sgn * v[pd]);
+            v[d] = m;
+            v[pd] = sgn * m;
+        }
+    }
+}
+
+// w -= shift * v  (the image of a correction under H - theta0)
+__global__ void k_shift_image(const double *v, double shift, int64_t N, double *w)
+{
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < N; d += (int64_t)gridDim.x * blockDim.x)
+        w[d] -= shift * v[d];
+}
+
+// Thick restart that keeps the anchor V[0], W[0]: u1 = sum_{i>=1} y_i V_i and
+// u2 = sum_{i>=1} y2_i V_i (the corrections of the two lowest Ritz vectors) and
+// their images.
+__global__ void k_anchor_restart(const double *V, const double *W, size_t ld, int m, const double *ys,
+                                 const double *y2s, int64_t N, double *u1, double *w1, double *u2, double *w2)
+{
+    double y[MLARGE], y2[MLARGE];
+#pragma unroll
+    for (int i = 0; i < MLARGE; ++i) {
+        y[i] = (i >= 1 && i < m) ? ys[i] : 0.0;
+        y2[i] = (i >= 1 && i < m) ? y2s[i] : 0.0;
+    }
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < N; d += (int64_t)gridDim.x * blockDim.x) {
+        double a = 0.0, b = 0.0, c = 0.0, e = 0.0;
+#pragma unroll
+        for (int i = 1; i < MLARGE; ++i) {
+            const double v = V[i * ld + d], w = W[i * ld + d];
+            a += y[i] * v;
+            b += y[i] * w;
+            c += y2[i] * v;
+            e += y2[i] * w;
+        }
+        u1[d] = a;
+        w1[d] = b;
+        u2[d] = c;
+        w2[d] = e;
+    }
+}
+
+// G entries of the anchored restart basis {V0, V1, V2} from dots = [W0.V1, V1.W1,
+// W0.V2, V1.W2, V2.W2] (G00 kept); two = 0 when V2 was dropped.
+__global__ void k_set_g3(double *Gd, const double *dots, int two)
+{
+    if (threadIdx.x == 0) {
+        Gd[1] = Gd[MMAX] = dots[0];
+        Gd[MMAX + 1] = dots[1];
+        if (two) {
+            Gd[2] = Gd[2 * MMAX] = dots[2];
+            Gd[MMAX + 2] = Gd[2 * MMAX + 1] = dots[3];
+            Gd[2 * MMAX + 2] = dots[4];
+        }
     }
 }
 
@@ -3252,23 +3906,48 @@ static int large_apply(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, con
 
 // One Davidson phase on the large space (T = sigma arithmetic).  D.x: start
 // vector in, Ritz vector out.
+// Anchored (anchor != NULL, T = float; see struct Anchor): D.x is the anchor x0;
+// one float64 sigma gives theta0 = x0.Hx0 and the exact image W0 = (H - theta0) x0
+// of V0 = x0; every later basis vector is a correction whose image is the float32
+// sigma minus theta0 times it; the coupling of x0 to V_m is formed as W0.V_m; a
+// thick restart keeps V0; *lambda returns theta0 + mu, *anchor_y0 the coefficient
+// of x0 in the Ritz vector (which is left in D.x, float64).
 template <typename T>
-static int large_phase(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, double tol, int min_iter,
-                       int max_iter, int steer, double *lambda, double *rnorm, int *nsig, int *status)
+static int large_phase(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, int sgn, double tol, int min_iter,
+                       int max_iter, int steer, double *lambda, double *rnorm, int *nsig, int *status,
+                       int *nsig64 = nullptr, double *anchor_y0 = nullptr)
 {
     const int64_t N = pl.L.N;
     const size_t ld = D.ld;
     cudaStream_t st = ctx->stream;
     const int g = pl.grid_vec;
-    double h3[3];
+    const bool anch = sizeof(T) == 4 && anchor_y0 != nullptr;
+    double h3[4];
     *nsig = 0;
     *status = MBE_STATUS_OK;
     int rc;
+    double shift = 0.0;
+    const int Ns = pl.L.Ns;
+    k_project_sector<<<g, 256, 0, st>>>(D.x, Ns, sgn, N);
     dot_to(ctx, pl, D, D.x, 1, D.x, D.dots);
     k_scale_copy<<<g, 256, 0, st>>>(D.x, nullptr, D.dots, N, D.V, nullptr, nullptr);
+    ctx->launches += 2;
+    if (anch) {
+        if ((rc = large_sigma_launch<double>(ctx, pl, D.V, D.W, pl.L.n))) return rc;
+        ++*nsig64;
+        k_project_sector<<<g, 256, 0, st>>>(D.W, Ns, sgn, N);
+        ++ctx->launches;
+        dot_to(ctx, pl, D, D.W, 1, D.V, D.dots);
+        MBE_CU(cudaMemcpyAsync(&shift, D.dots, 8, cudaMemcpyDeviceToHost, st));
+        MBE_CU(cudaStreamSynchronize(st));
+        k_shift_image<<<g, 256, 0, st>>>(D.V, shift, N, D.W);
+        ++ctx->launches;
+    } else {
+        if ((rc = large_apply<T>(ctx, pl, D, D.V, D.W))) return rc;
+        ++*nsig;
+    }
+    k_project_sector<<<g, 256, 0, st>>>(D.W, Ns, sgn, N);
     ++ctx->launches;
-    if ((rc = large_apply<T>(ctx, pl, D, D.V, D.W))) return rc;
-    ++*nsig;
     dot_to(ctx, pl, D, D.W, 1, D.V, D.dots);
     k_set_g2<<<1, 32, 0, st>>>(D.Gd, D.dots, 0);
     ++ctx->launches;
@@ -3278,16 +3957,21 @@ static int large_phase(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, dou
     for (int it = 0;; ++it) {
         k_large_small_eig<<<1, 32, 0, st>>>(D.Gd, m, D.ys, D.y2s, D.misc);
         double *tdst = (m < MLARGE) ? D.V + (size_t)m * ld : D.t;
-        k_ritz<<<D.nblk, LARGE_THREADS, 0, st>>>(D.V, D.W, ld, m, D.ys, D.misc, pl.L.diag, N, D.x, D.hx, tdst,
-                                                 D.partial);
+        k_ritz<<<D.nblk, LARGE_THREADS, 0, st>>>(D.V, D.W, ld, m, D.ys, D.misc, pl.L.diag, shift, N, D.x, D.hx,
+                                                 tdst, D.partial);
         k_multidot_final<<<1, 64, 0, st>>>(D.partial, D.nblk, 2, D.dots);
         ctx->launches += 3;
+        int herr = 0;
         MBE_CU(cudaMemcpyAsync(h3, D.dots, 16, cudaMemcpyDeviceToHost, st));
         MBE_CU(cudaMemcpyAsync(h3 + 2, D.misc, 8, cudaMemcpyDeviceToHost, st));
+        MBE_CU(cudaMemcpyAsync(h3 + 3, D.ys, 8, cudaMemcpyDeviceToHost, st));
+        MBE_CU(cudaMemcpyAsync(&herr, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         MBE_CU(cudaStreamSynchronize(st));
+        if (herr) return check_dev_err(ctx);
         const double rn = sqrt(h3[0]), t0n = sqrt(h3[1]);
-        *lambda = h3[2];
+        *lambda = shift + h3[2];
         *rnorm = rn;
+        if (anch) *anchor_y0 = h3[3];
         if (!std::isfinite(rn) || !std::isfinite(h3[2])) {
             *status = MBE_STATUS_NONFINITE;
             break;
@@ -3306,7 +3990,43 @@ static int large_phase(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, dou
             }
         }
         double *u = D.V + (size_t)m * ld;
-        if (m == MLARGE) {
+        if (m == MLARGE && anch) {
+            // keep V0 = x0, W0 = r0; V1, V2: corrections of the two lowest Ritz vectors
+            // (D.t holds the new correction; D.x, D.hx are recomputed by the next k_ritz)
+            k_anchor_restart<<<g, 256, 0, st>>>(D.V, D.W, ld, m, D.ys, D.y2s, N, D.x2, D.hx2, D.x, D.hx);
+            k_copy2<<<g, 256, 0, st>>>(D.x2, D.hx2, N, D.V + ld, D.W + ld);
+            ctx->launches += 2;
+            dot_to(ctx, pl, D, D.V + ld, 1, D.V + ld, D.dots);
+            k_scale_copy<<<g, 256, 0, st>>>(D.V + ld, D.W + ld, D.dots, N, D.V + ld, D.W + ld, nullptr);
+            k_copy2<<<g, 256, 0, st>>>(D.x, D.hx, N, D.V + 2 * ld, D.W + 2 * ld);
+            ctx->launches += 2;
+            for (int pass = 0; pass < 2; ++pass) {
+                dot_to(ctx, pl, D, D.V + ld, 1, D.V + 2 * ld, D.dots);
+                k_subtract<<<g, 256, 0, st>>>(D.V + ld, D.W + ld, ld, 1, D.dots, N, D.V + 2 * ld, D.W + 2 * ld);
+                ++ctx->launches;
+            }
+            dot_to(ctx, pl, D, D.V + 2 * ld, 1, D.V + 2 * ld, D.dots);
+            MBE_CU(cudaMemcpyAsync(h3, D.dots, 8, cudaMemcpyDeviceToHost, st));
+            MBE_CU(cudaStreamSynchronize(st));
+            const int two = sqrt(h3[0]) > 1e-3 ? 1 : 0;
+            if (two) {
+                k_scale_copy<<<g, 256, 0, st>>>(D.V + 2 * ld, D.W + 2 * ld, D.dots, N, D.V + 2 * ld, D.W + 2 * ld,
+                                                 nullptr);
+                ++ctx->launches;
+            }
+            dot_to(ctx, pl, D, D.W, 1, D.V + ld, D.dots);               // W0.V1
+            dot_to(ctx, pl, D, D.V + ld, 1, D.W + ld, D.dots + 1);      // V1.W1
+            if (two) {
+                dot_to(ctx, pl, D, D.W, 1, D.V + 2 * ld, D.dots + 2);   // W0.V2
+                dot_to(ctx, pl, D, D.V + ld, 1, D.W + 2 * ld, D.dots + 3);  // V1.W2
+                dot_to(ctx, pl, D, D.V + 2 * ld, 1, D.W + 2 * ld, D.dots + 4);  // V2.W2
+            }
+            k_set_g3<<<1, 32, 0, st>>>(D.Gd, D.dots, two);
+            ++ctx->launches;
+            m = 2 + two;
+            u = D.V + (size_t)m * ld;
+            MBE_CU(cudaMemcpyAsync(u, D.t, (size_t)N * 8, cudaMemcpyDeviceToDevice, st));
+        } else if (m == MLARGE) {
             // thick restart on the two lowest Ritz vectors (orthogonal by construction)
             k_lincomb2<<<g, 256, 0, st>>>(D.V, D.W, ld, m, D.y2s, N, D.x2, D.hx2);
             k_copy2<<<g, 256, 0, st>>>(D.x, D.hx, N, D.V, D.W);
@@ -3327,6 +4047,8 @@ static int large_phase(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, dou
             u = D.V + (size_t)m * ld;
             MBE_CU(cudaMemcpyAsync(u, D.t, (size_t)N * 8, cudaMemcpyDeviceToDevice, st));
         }
+        k_project_sector<<<g, 256, 0, st>>>(u, Ns, sgn, N);
+        ++ctx->launches;
         for (int pass = 0; pass < 2; ++pass) {
             dot_to(ctx, pl, D, D.V, m, u, D.dots);
             k_subtract<<<g, 256, 0, st>>>(D.V, nullptr, ld, m, D.dots, N, u, nullptr);
@@ -3344,7 +4066,14 @@ static int large_phase(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, dou
         ++ctx->launches;
         if ((rc = large_apply<T>(ctx, pl, D, u, D.W + (size_t)m * ld))) return rc;
         ++*nsig;
+        k_project_sector<<<g, 256, 0, st>>>(D.W + (size_t)m * ld, Ns, sgn, N);
+        ++ctx->launches;
+        if (anch) {
+            k_shift_image<<<g, 256, 0, st>>>(u, shift, N, D.W + (size_t)m * ld);
+            ++ctx->launches;
+        }
         dot_to(ctx, pl, D, D.V, m + 1, D.W + (size_t)m * ld, D.dots);
+        if (anch) dot_to(ctx, pl, D, D.W, 1, u, D.dots);  // x0.(A u) as u.r0
         k_set_gcol<<<1, 32, 0, st>>>(D.Gd, m, D.dots);
         ++ctx->launches;
         ++m;
@@ -3415,6 +4144,7 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
     ctx->launches += 2;
     double lam = 0.0, rn = 0.0;
     int n32 = 0, n64 = 0, st = 0;
+    bool degen = false;
     // the two spin-flip sectors (see sector_guess); each runs the float32 phase
     // (mixed mode) and the float64 phase; the second sector first runs a float64
     // pass to the residual SECTOR_TOL only and stops there when sector_loses
@@ -3426,31 +4156,54 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
         ++ctx->launches;
         double l = 0.0, r = 0.0;
         int s64 = 0, s32 = 0, ss = MBE_STATUS_OK;
-        bool lose = false;
-        if (sector == 1) {
-            // a float64 pass from the start vector to SECTOR_TOL decides (a float32
-            // pass of this slowly converging solver stalls short of it)
+        bool lose = false, refined = false;
+        if (mixed) {
+            // float32 phase (tensor-core sigma), then anchored refinements (struct
+            // Anchor): one float64 sigma per anchor, float32 sigmas for the
+            // corrections; the second sector is decided once its residual reaches
+            // SECTOR_TOL. A refinement that fails hands over to the float64 phase.
             int n = 0;
-            rc = large_phase<double>(ctx, pl, D, SECTOR_TOL, 0, o.max_iter, LARGE_STALL, &l, &r, &n, &ss);
+            rc = large_phase<float>(ctx, pl, D, sgn, o.tol_switch, 0, o.max_iter, 3, &l, &r, &n, &ss);
+            if (rc) return rc;
+            s32 += n;
+            bool decided = sector == 0;
+            if (ss == MBE_STATUS_NONFINITE) {
+                k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best + sector, Ns, sgn, N, D.x);
+                ++ctx->launches;
+            } else {
+                for (int anc = 0; anc < LARGE_ANCHORS && !lose && !refined; ++anc) {
+                    const double tgt = decided ? o.tol : SECTOR_TOL;
+                    double y0 = 1.0;
+                    int n64a = 0;
+                    n = 0;
+                    rc = large_phase<float>(ctx, pl, D, sgn, tgt, decided ? o.fp64_final_iters : 0, o.max_iter,
+                                            LARGE_ANCHOR_STALL, &l, &r, &n, &ss, &n64a, &y0);
+                    if (rc) return rc;
+                    s32 += n;
+                    s64 += n64a;
+                    if (ss == MBE_STATUS_NONFINITE) break;
+                    if (!decided && r <= SECTOR_TOL) {
+                        decided = true;
+                        lose = sector_loses(l, r, lam, 0.0);
+                        continue;
+                    }
+                    const double dn = sqrt(std::max(0.0, 1.0 - y0 * y0)) / std::max(fabs(y0), 1e-300);
+                    refined = decided && r <= o.tol && dn <= MIX_DMAX;
+                }
+            }
+        } else if (sector == 1) {
+            // a float64 pass from the start vector to SECTOR_TOL decides
+            int n = 0;
+            rc = large_phase<double>(ctx, pl, D, sgn, SECTOR_TOL, 0, o.max_iter, LARGE_STALL, &l, &r, &n, &ss);
             if (rc) return rc;
             s64 += n;
             lose = ss == MBE_STATUS_NONFINITE || sector_loses(l, r, lam, 0.0);
         }
-        // (the second sector, when it may lie lower, goes on in float64 from its
-        // deciding pass, as in float64 mode)
-        if (!lose && mixed && sector == 0) {
-            rc = large_phase<float>(ctx, pl, D, o.tol_switch, 0, o.max_iter, 3, &l, &r, &s32, &ss);
-            if (rc) return rc;
-            if (ss == MBE_STATUS_NONFINITE) {
-                k_large_guess<<<pl.grid_vec, 256, 0, ctx->stream>>>(D.best + sector, Ns, sgn, N, D.x);
-                ++ctx->launches;
-            }
-        }
-        if (!lose) {
+        if (refined) ss = MBE_STATUS_OK;
+        if (!lose && !refined) {
             int n = 0;
-            rc = large_phase<double>(ctx, pl, D, o.tol, (mixed && sector == 0) ? o.fp64_final_iters : 0, o.max_iter, 0,
-                                     &l, &r, &n,
-                                     &ss);
+            rc = large_phase<double>(ctx, pl, D, sgn, o.tol, (mixed && sector == 0) ? o.fp64_final_iters : 0,
+                                     o.max_iter, 0, &l, &r, &n, &ss);
             if (rc) return rc;
             s64 += n;
         }
@@ -3461,10 +4214,12 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
             rn = r;
             st = ss;
         } else if (!lose && ss != MBE_STATUS_NONFINITE && l < lam) {
+            degen = degen || (ss == MBE_STATUS_OK && st == MBE_STATUS_OK && fabs(l - lam) <= DEGEN_TOL);
             lam = l;
             rn = r;
             st = ss;
         } else {
+            degen = degen || (!lose && ss == MBE_STATUS_OK && st == MBE_STATUS_OK && fabs(l - lam) <= DEGEN_TOL);
             MBE_CU(cudaMemcpyAsync(D.x, D.xs, (size_t)N * 8, cudaMemcpyDeviceToDevice, ctx->stream));
         }
     }
@@ -3475,7 +4230,7 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
     result[0] = lam;
     result[1] = lam - ephi;
     result[2] = rn;
-    info[0] = st;
+    info[0] = with_degeneracy(st, degen);
     info[1] = n64;
     info[2] = n32;
     return MBE_OK;

@@ -95,6 +95,7 @@ struct mbe_ctx {
     void *ws = nullptr;
     size_t ws_size = 0;
     mbe::StringTable tables[MBE_MAX_STRING_ORB + 1][MBE_MAX_STRING_ORB + 1];
+    int *dev_err = nullptr;  // device flag set by a kernel whose bounded wait ran out
     int64_t launches = 0;  // kernels launched by this context
     bool timing = false;
     struct Pending {
@@ -112,6 +113,10 @@ int workspace(mbe_ctx *ctx, size_t bytes, void **out);
 
 // Cached device string table of class (n, k); builds it on first use.
 int get_table(mbe_ctx *ctx, int n, int k, const StringTable **out);
+
+// Reads and clears the context's device error flag (synchronous); MBE_ECUDA with a
+// message when a kernel's bounded wait ran out.
+int check_dev_err(mbe_ctx *ctx);
 
 // Bump allocator over a workspace region.
 struct Bump {
@@ -152,5 +157,13 @@ __device__ inline int64_t find_tuple(const int32_t *list, int64_t len, int m, co
 
 // Exclusive scan of per-block counts into offsets[0..nblocks] (one block).
 __global__ void k_scan_counts(const int32_t *counts, int64_t nblocks, int64_t *offsets);
+
+// The opposite-spin term of one large active space's float32 sigma on the tensor
+// cores (large_tc.cu): sigma[Ia][*] written for every alpha string Ia from the
+// float32 coefficients c [Ns][Ns], the replacement lists tab [Ns][R] and the
+// float32 packed-pair integrals V32 [P][P].  *err (device) is set to 1 if a
+// bounded wait runs out.
+int large_ab_tc(cudaStream_t st, int sm_count, size_t smem_optin, int P, int Ns, int R, const int32_t *tab,
+                const float *V32, const float *c, double *sigma, int *err);
 
 }  // namespace mbe

@@ -75,6 +75,19 @@ __global__ void k_string_table(int n, int k, int64_t ns, int r, uint32_t *string
     }
 }
 
+int check_dev_err(mbe_ctx *ctx)
+{
+    int h = 0;
+    MBE_CU(cudaMemcpyAsync(&h, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    MBE_CU(cudaStreamSynchronize(ctx->stream));
+    if (h) {
+        MBE_CU(cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), ctx->stream));
+        set_error("a kernel's bounded wait on its tensor-core work ran out (results discarded)");
+        return MBE_ECUDA;
+    }
+    return MBE_OK;
+}
+
 int get_table(mbe_ctx *ctx, int n, int k, const StringTable **out)
 {
     MBE_CHECK(n >= 0 && n <= MBE_MAX_STRING_ORB && k >= 0 && k <= n, MBE_EUNSUPPORTED,
@@ -113,7 +126,7 @@ void mbe_default_opts(mbe_opts *o)
 {
     if (!o) return;
     o->precision = MBE_PREC_FP64;
-    o->tol = 1e-6;
+    o->tol = 1e-7;
     o->tol_switch = 1e-5;
     o->max_iter = 2000;
     o->fp64_final_iters = 2;
@@ -142,6 +155,13 @@ int mbe_ctx_create(mbe_ctx **ctx, int device, void *cuda_stream)
     }
     c->sm_count = prop.multiProcessorCount;
     c->smem_optin = prop.sharedMemPerBlockOptin;
+    e = cudaMalloc(&c->dev_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->dev_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        if (c->dev_err) cudaFree(c->dev_err);
+        delete c;
+        return cuda_fail(e, "mbe_ctx_create: error flag", __FILE__, __LINE__);
+    }
     *ctx = c;
     return MBE_OK;
 }
@@ -159,7 +179,7 @@ int mbe_ctx_sync(mbe_ctx *ctx)
     MBE_CU(cudaSetDevice(ctx->device));
     MBE_CU(cudaStreamSynchronize(ctx->stream));
     MBE_CU(cudaGetLastError());
-    return MBE_OK;
+    return check_dev_err(ctx);
 }
 
 void mbe_ctx_destroy(mbe_ctx *ctx)
@@ -178,6 +198,7 @@ void mbe_ctx_destroy(mbe_ctx *ctx)
             if (ctx->tables[n][k].table) cudaFree(ctx->tables[n][k].table);
         }
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->dev_err) cudaFree(ctx->dev_err);
     delete ctx;
 }
 

@@ -108,7 +108,7 @@ def test_casci_solve_hubbard8_full_space(eng, ctx, prec):
     assert abs(res["lam"] - exact) < 1e-9
     assert abs(res["eps"] - (exact - omb.phi_energy(h1, eri, occ))) < 1e-9
     if prec == "mixed":
-        assert res["n32"] > 0 and res["n64"] >= 3
+        assert res["n32"] > 0 and res["n64"] >= 1  # float64 sigmas: one per anchor
 
 
 def test_casci_solve_molecule_12o_row_sampled_residual(eng, ctx, molecule):

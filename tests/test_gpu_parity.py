@@ -1,9 +1,9 @@
 """Parity of the CUDA path (through the C ABI) with the oracle.
 
 Bit-exact: tuple lists, string tables and addressing.  Floating point: sigma
-element by element (1e-11 relative to the largest |sigma|), tuple energies
-within 1e-9 E_h in float64 mode and 1e-8 E_h in mixed mode, increments within
-4x those (an increment sums up to 2^n - 1 tuple energies).
+element by element (1e-11 relative to the largest |sigma|); tuple energies,
+increments and totals within 1e-9 E_h in float64 mode and 1e-8 E_h in mixed
+mode, except where a test states a wider bound and its reason.
 """
 
 import itertools
@@ -151,12 +151,12 @@ def test_full_mbe_hubbard8(eng, ctx, prec):
         assert np.abs(eps - want).max() <= tol, (n, np.abs(eps - want).max())
         inc = out["inc"][i].cpu().numpy()
         want_i = np.array([ref["inc"][t] for t in tup])
-        assert np.abs(inc - want_i).max() <= 4 * tol
+        assert np.abs(inc - want_i).max() <= tol
     e_order = out["e_order"].cpu().numpy()
     for i, n in enumerate(w.orders):
-        assert abs(e_order[i] - ref["e_order"][n]) <= 16 * tol
+        assert abs(e_order[i] - ref["e_order"][n]) <= tol
     fci_e = fci.lowest_eigenvalue(w.h1, w.eri, 4, 4)
-    assert abs(float(out["e_total"].item()) - fci_e) <= 32 * tol
+    assert abs(float(out["e_total"].item()) - fci_e) <= tol
     assert abs(float(out["e_phi"].item()) - ref["e_phi"]) <= 1e-12
 
 
@@ -174,7 +174,7 @@ def test_mbe_with_reference_space(eng, ctx, prec):
         eps = out["eps"][i].cpu().numpy()
         want = np.array([ref["eps"][n][t] for t in tup])
         assert np.abs(eps - want).max() <= TOL[prec]
-    assert abs(float(out["e_total"].item()) - ref["e_tot"]) <= 16 * TOL[prec]
+    assert abs(float(out["e_total"].item()) - ref["e_tot"]) <= TOL[prec]
 
 
 def _sampled_increments(w, tuples_by_order, eps_by_order, inc_by_order, order, rng, nsample, prec):
@@ -205,7 +205,7 @@ def _sampled_increments(w, tuples_by_order, eps_by_order, inc_by_order, order, r
         worst_e = max(worst_e, abs(gpu_eps[i] - sub_eps[order][t]))
         worst_i = max(worst_i, abs(gpu_inc[i] - inc[t]))
     assert worst_e <= TOL[prec], worst_e
-    assert worst_i <= 4 * TOL[prec], worst_i
+    assert worst_i <= TOL[prec], worst_i
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])

@@ -125,3 +125,43 @@ def test_even_sector_targeting(eng, ctx, system, prec):
     res = ctx.casci_solve(dev(h1), dev(eri), dev(occ), list(ODD), eng.Opts(precision=prec, tol=1e-7, even_only=True))
     assert res["status"] == 0
     assert abs(res["lam"] - fci.lowest_eigenvalue_even(he, ea, k)) < 1e-9
+
+
+def _decoupled_sites(n_pairs=2, U=4.0):
+    """Sites without hopping, doubly occupied ones below the empty ones: in a tuple
+    {i, a} (one occupied, one empty site) the two determinants with one electron on
+    each site, |i alpha, a beta> and |a alpha, i beta>, are uncoupled eigenstates of
+    equal energy h_ii + h_aa, below the doubly occupied ones (h_ii < h_aa < h_ii + U).
+    Their even and odd combinations, the lowest states of the two spin-flip
+    sectors, are exactly degenerate."""
+    n = 2 * n_pairs
+    h1 = np.diag(np.concatenate([np.linspace(-1.0, -0.8, n_pairs), np.linspace(0.0, 0.3, n_pairs)]))
+    eri = np.zeros((n,) * 4)
+    for i in range(n):
+        eri[i, i, i, i] = U
+    occ = np.array([1] * n_pairs + [0] * n_pairs, dtype=np.uint8)
+    return h1, eri, occ
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_degenerate_ground_state_is_flagged(eng, ctx, prec):
+    h1, eri, occ = _decoupled_sites()
+    e_phi = omb.phi_energy(h1, eri, occ)
+    tup = [(0, 2), (0, 3), (1, 2)]
+    eps, st, _ = ctx.casci_batch(dev(h1), dev(eri), dev(occ), [], 0.0, 2,
+                                 torch.tensor(tup, dtype=torch.int32, device="cuda"), eng.Opts(precision=prec))
+    assert st.cpu().tolist() == [4, 4, 4]  # MBE_STATUS_DEGENERATE: the energy is still valid
+    want = [omb.tuple_energy(h1, eri, occ, [], t, e_phi, 0.0) for t in tup]
+    assert np.abs(eps.cpu().numpy() - np.array(want)).max() <= 1e-9
+    # the same space through the single large-CAS solver
+    res = ctx.casci_solve(dev(h1), dev(eri), dev(occ), [0, 2], eng.Opts(precision=prec))
+    assert res["status"] == 4 and abs(res["eps"] - want[0]) <= 1e-9
+
+
+def test_nondegenerate_ground_state_is_not_flagged(eng, ctx):
+    h1, eri, occ = _decoupled_sites()
+    h1 = h1.copy()
+    h1[0, 2] = h1[2, 0] = 0.05  # hopping lifts the singlet-triplet degeneracy
+    eps, st, _ = ctx.casci_batch(dev(h1), dev(eri), dev(occ), [], 0.0, 2,
+                                 torch.tensor([(0, 2)], dtype=torch.int32, device="cuda"))
+    assert st.item() == 0

@@ -52,7 +52,7 @@ def test_default_opts_without_gpu(libpath):
     from paper_1910_03527_gb300.binding import MbeOpts, lib
     o = MbeOpts()
     lib().mbe_default_opts(ctypes.byref(o))
-    assert o.precision == 0 and o.tol == 1e-6 and o.max_iter == 2000 and o.fp64_final_iters == 2 and o.sectors == 0
+    assert o.precision == 0 and o.tol == 1e-7 and o.max_iter == 2000 and o.fp64_final_iters == 2 and o.sectors == 0
 
 
 def test_count_query_needs_no_gpu(libpath):

@@ -34,13 +34,14 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def _noalloc(lib, h1, eri, occ, A, k, c):
+def _noalloc(lib, h1, eri, occ, A, k, c, want_diag=True):
     sigma = torch.empty_like(c)
-    diag = torch.empty_like(c)
+    diag = torch.empty_like(c) if want_diag else None
     A_h = (ctypes.c_int32 * len(A))(*A)
     stream = torch.cuda.current_stream()
     rc = lib.casci_sigma_noalloc(0, ctypes.c_void_p(stream.cuda_stream), h1.shape[0], _ptr(h1), _ptr(eri),
-                                 _ptr(occ), len(A), A_h, k, _ptr(c), _ptr(sigma), _ptr(diag))
+                                 _ptr(occ), len(A), A_h, k, _ptr(c), _ptr(sigma),
+                                 _ptr(diag) if diag is not None else None)
     return rc, sigma, diag
 
 
@@ -81,3 +82,34 @@ def test_noalloc_rejects_problems_beyond_its_limit():
     rc, _, _ = _noalloc(lib, th1, teri, tocc, list(range(11)), 5, c)
     assert rc == -4
     assert "allocation-free limit" in lib.mbe_last_error().decode()
+
+
+def test_noalloc_diagonal_in_scratch_and_explicit_sector():
+    """Two paths the casci_sigma comparison cannot reach: the diagonal kept in the
+    fixed array (diag NULL; the 10-orbital, 5-electron space, the largest within
+    the limit of 10 orbitals, needs about 1.1 MB of the 2 MiB), and an electron
+    count other than the reference occupation gives
+    (n_el = 2 in a space whose occupied count is 3), checked against the oracle's
+    sigma of that sector."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1910_03527_gb300 as eng
+    from oracle import fci
+    eng.build()
+    lib = eng.lib()
+    h1, eri, occ = random_system(12, 6, seed=23)
+    th1, teri, tocc = _dev(h1), _dev(eri), _dev(occ)
+    for A, k in ((list(range(1, 11)), 5), ([1, 3, 4, 6, 8, 9], 2)):
+        ndet = math.comb(len(A), k) ** 2
+        c = _dev(np.random.default_rng(k).normal(size=ndet))
+        rc, got, _ = _noalloc(lib, th1, teri, tocc, A, k, c, want_diag=False)
+        assert rc == 0, lib.mbe_last_error().decode()
+        torch.cuda.synchronize()
+        e_core, h_eff, eri_a = omb.frozen_core(h1, eri, occ, A)
+        if ndet <= 50_000:
+            want = fci.sigma(h_eff, eri_a, k, k, c.cpu().numpy())
+            assert np.abs(got.cpu().numpy() - want).max() <= 1e-11 * np.abs(want).max()
+        else:
+            rows = np.random.default_rng(5).choice(ndet, size=300, replace=False)
+            want = fci.sigma_rows(h_eff, eri_a, k, k, c.cpu().numpy(), rows)
+            assert np.abs(got.cpu().numpy()[rows] - want).max() <= 1e-11 * np.abs(want).max()
