@@ -276,6 +276,37 @@ def cpu_baseline_entry(res, one=None):
 
 # ----------------------------------------------------------------------------- our arm
 
+def autotune_orders(ctx, eng, w, h1, eri, occ, opts_list):
+    """mbe_autotune on every order of the workload, in each precision, before the
+    timed steps: the library times the candidate launch choices on that order's
+    whole tuple list (best of two runs after a warm-up) and keeps the fastest on
+    the context.  Returns, per precision and order, the choice and the timed
+    launch of the default choice next to the tuned one."""
+    occ_host = w.occ.tolist()
+    table = {}
+    for opts in opts_list:
+        prec = opts.precision
+        rows = {}
+        for order in w.orders:
+            tup = ctx.mbe_tuples(w.norb, occ_host, w.exp, w.ref, order, w.skip)
+            if tup.shape[0] == 0:
+                continue
+            default = ctx.get_tuning(prec, len(w.ref) + order)
+            best, recs = ctx.autotune(h1, eri, occ, w.ref, 0.0, order, tup, opts)
+            ms_default = next((ms for t, ms in recs if t == default), None)
+            ms_best = min(ms for _, ms in recs)
+            rows[str(order)] = {"tuples": int(tup.shape[0]), "choice": best, "default": default,
+                                "ms_default": ms_default, "ms_tuned": ms_best,
+                                "candidates": [[t["warp_max_ndet"], t["warp_warps"], t["block_basis"], ms]
+                                               for t, ms in recs]}
+        table[prec] = rows
+    table["method"] = ("mbe_autotune per order: candidates warp_max_ndet {100, 225, 416}, warps per block "
+                       "{2, 4}, block basis {12, 16, 20}, each field in turn with the others at their best "
+                       "so far; one casci_batch over the order's tuples per candidate, best of 2 after a "
+                       "warm-up, CUDA events")
+    return table
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -312,6 +343,12 @@ def run_ours(args):
         step(mixed)
         step(fp64)
     torch.cuda.synchronize()
+    tuning = None if args.no_autotune else autotune_orders(ctx, eng, w, h1, eri, occ, (mixed, fp64))
+    if tuning is not None:
+        for _ in range(2):  # the tuned launch shapes warmed up too
+            step(mixed)
+            step(fp64)
+        torch.cuda.synchronize()
 
     def timed(opts):
         barrier()
@@ -461,6 +498,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "alu_peaks_tflops": peaks,
+        "autotune": tuning,
     }
     if rank == 0 and not args.no_cpu_baseline:
         one = run_oracle_subprocess(args.cpu_seconds / 2, 1)
@@ -527,7 +565,7 @@ def run_ncu_case(args):
         eps, st, it = ctx.casci_batch(h1, eri, occ, w.ref, 0.0, args.ncu_order, tup, opts)
     torch.cuda.synchronize()
     print(json.dumps({"case": args.ncu_case, "order": args.ncu_order, "tuples": int(tup.shape[0]),
-                      "non_ok": int((st != 0).sum().item())}))
+                      "non_ok": int(((st >= 1) & (st <= 3)).sum().item())}))
     ctx.close()
 
 
@@ -634,7 +672,7 @@ def run_screened(args):
                        "(T_init = 1e-10, M_init = 3, a = 5)",
            "tuples_per_order": counts, "unscreened_tuples_per_order": full,
            "e_total": float(out["e_total"].item()),
-           "non_ok_status": int(sum(int((s != 0).sum()) for s in out["status"])),
+           "non_ok_status": int(sum(int(((s >= 1) & (s <= 3)).sum()) for s in out["status"])),
            "clock": "host wall clock around the whole pass (one stream synchronisation per order)"}
     print(json.dumps(res))
     ctx.close()
@@ -690,7 +728,7 @@ def run_expansion(args):
                        f"orders 1-{args.expansion_max_order}",
            "per_order": per_order, "e_total": float(out["e_total"].item()),
            "e_ref_corr": float(out["e_ref_corr"]),
-           "non_ok_status": int(sum(int((st != 0).sum()) for st in out["status"])),
+           "non_ok_status": int(sum(int(((st >= 1) & (st <= 3)).sum()) for st in out["status"])),
            "clock": "host wall clock around the whole pass"}
     print(json.dumps(res))
     ctx.close()
@@ -738,7 +776,7 @@ def run_molecule(args):
             per_order[n] = {"tuples": nt, "solver_ms": ms, "solves_per_s": nt / (ms / 1e3) if ms > 0 else None,
                             "fp64_sigma_per_tuple": float(((it >> 16) & 0xffff).double().mean().item()) if nt else 0,
                             "fp32_sigma_per_tuple": float((it & 0xffff).double().mean().item()) if nt else 0,
-                            "non_ok": int((res["status"][i] != 0).sum().item())}
+                            "non_ok": int(((res["status"][i] >= 1) & (res["status"][i] <= 3)).sum().item())}
         n_t = sum(v["tuples"] for v in per_order.values())
         out["per_precision"][prec] = {"value": n_t / t, "seconds": t, "e_total": e_tot, "per_order": per_order}
     print(json.dumps(out))
@@ -811,6 +849,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the default launch choices instead of tuning them per order in the warm-up")
     ap.add_argument("--oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-shard", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-shards", type=int, default=1, help=argparse.SUPPRESS)

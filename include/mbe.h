@@ -142,6 +142,43 @@ typedef struct mbe_timing {
 int mbe_ctx_set_timing(mbe_ctx *ctx, int enable);
 int mbe_ctx_timings(mbe_ctx *ctx, int max, mbe_timing *out, int *count);
 
+/* Launch choices of casci_batch, chosen per precision and active-space size (the
+   paper names no solver shapes; these are the engine's own):
+     warp_max_ndet  tuple spaces of at most this many determinants (and at most 8
+                    orbitals) run one per warp with the Davidson vectors in registers,
+                    the others one per thread block (1..416; default 416)
+     warp_warps     warps per thread block of the warp solver (1..4; default 4)
+     block_basis    Davidson basis of the block solver (4..20; default 20)       */
+typedef struct mbe_tuning {
+    int warp_max_ndet;
+    int warp_warps;
+    int block_basis;
+} mbe_tuning;
+
+/* Sets the tuning of later casci_batch calls for one precision (MBE_PREC_*) and
+   active-space size n_cas = |R| + order (1..MBE_MAX_CAS), or for every size when
+   n_cas is 0; reads it back.  Host only.  Errors: MBE_EINVAL (values out of range). */
+int mbe_ctx_set_tuning(mbe_ctx *ctx, int precision, int n_cas, const mbe_tuning *t);
+int mbe_ctx_get_tuning(const mbe_ctx *ctx, int precision, int n_cas, mbe_tuning *t);
+
+/* Autotuner of the launch choices: runs casci_batch (same arguments; outputs into
+   its own temporary buffers) on the given tuples, typically a sample of one order,
+   for candidates of each tuning field in turn, starting from the current tuning:
+   warp_warps in {2, 4}, then warp_max_ndet in {100, 225, 416}, then block_basis in
+   {12, 16, 20}; each candidate is timed (CUDA events, best of two calls after one
+   warm-up call) and the fastest kept.  The result is set on the context for this
+   precision and |R| + order and returned in *best; records[0..*n_records) (host,
+   up to max_records) list every candidate with its time.  Synchronous.
+   Errors: as casci_batch. */
+typedef struct mbe_tune_record {
+    mbe_tuning tuning;
+    float ms;
+} mbe_tune_record;
+int mbe_autotune(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ, int n_ref,
+                 const int32_t *ref_orbs, double e_ref_corr, int order, int64_t n_tuples, const int32_t *tuples,
+                 const mbe_opts *opts, mbe_tuning *best, mbe_tune_record *records, int max_records,
+                 int *n_records);
+
 /* Measurement helper, not part of the method: the fused multiply-add throughput
    of the context's GPU, the denominator of the roofline fraction of the solver
    kernels (which are bound by plain float64 / float32 arithmetic).  Runs one

@@ -32,7 +32,8 @@ EXPORTS = ("mbe_default_opts", "mbe_ctx_create", "mbe_ctx_set_stream", "mbe_ctx_
            "mbe_ctx_timings", "mbe_tuples", "mbe_string_table", "mbe_phi_energy",
            "casci_batch", "casci_sigma", "casci_sigma_noalloc", "mbe_increments", "mbe_total",
            "mbe_weights", "casci_rdm_batch", "mbe_phi_gradient", "casci_sigma_large", "casci_solve",
-           "mbe_screen", "casci_batch_routed", "mbe_fma_peak")
+           "mbe_screen", "casci_batch_routed", "mbe_fma_peak", "mbe_ctx_set_tuning", "mbe_ctx_get_tuning",
+           "mbe_autotune")
 
 
 class MbeOpts(ctypes.Structure):
@@ -44,6 +45,14 @@ class MbeOpts(ctypes.Structure):
 class MbeTiming(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("solver", ctypes.c_int), ("dpl", ctypes.c_int),
                 ("ms", ctypes.c_float)]
+
+
+class MbeTuning(ctypes.Structure):
+    _fields_ = [("warp_max_ndet", ctypes.c_int), ("warp_warps", ctypes.c_int), ("block_basis", ctypes.c_int)]
+
+
+class MbeTuneRecord(ctypes.Structure):
+    _fields_ = [("tuning", MbeTuning), ("ms", ctypes.c_float)]
 
 
 class MbeError(RuntimeError):
@@ -111,6 +120,13 @@ def lib() -> ctypes.CDLL:
     L.casci_batch_routed.restype = i32
     L.casci_batch_routed.argtypes = [P, i32, P, P, P, i32, P, dbl, i32, i64, P, ctypes.POINTER(MbeOpts), i64,
                                      P, P, P]
+    L.mbe_ctx_set_tuning.restype = i32
+    L.mbe_ctx_set_tuning.argtypes = [P, i32, i32, ctypes.POINTER(MbeTuning)]
+    L.mbe_ctx_get_tuning.restype = i32
+    L.mbe_ctx_get_tuning.argtypes = [P, i32, i32, ctypes.POINTER(MbeTuning)]
+    L.mbe_autotune.restype = i32
+    L.mbe_autotune.argtypes = [P, i32, P, P, P, i32, P, dbl, i32, i64, P, ctypes.POINTER(MbeOpts),
+                               ctypes.POINTER(MbeTuning), ctypes.POINTER(MbeTuneRecord), i32, ctypes.POINTER(i32)]
     L.mbe_fma_peak.restype = i32
     L.mbe_fma_peak.argtypes = [P, i32, i32, ctypes.POINTER(dbl)]
     L.mbe_screen.restype = i32
@@ -210,6 +226,40 @@ class Context:
         _check(lib().mbe_fma_peak(self._h, {"fp64": 0, "fp32": 1}[kind], int(reps), ctypes.byref(out)),
                "mbe_fma_peak")
         return out.value
+
+    @staticmethod
+    def _tuning_dict(t: MbeTuning) -> dict:
+        return dict(warp_max_ndet=t.warp_max_ndet, warp_warps=t.warp_warps, block_basis=t.block_basis)
+
+    def set_tuning(self, precision: str, n_cas: int, warp_max_ndet: int, warp_warps: int, block_basis: int) -> None:
+        """Launch choices of later casci_batch calls (n_cas 0: every active-space size)."""
+        t = MbeTuning(warp_max_ndet, warp_warps, block_basis)
+        _check(lib().mbe_ctx_set_tuning(self._h, {"fp64": MBE_PREC_FP64, "mixed": MBE_PREC_MIXED}[precision],
+                                        int(n_cas), ctypes.byref(t)), "mbe_ctx_set_tuning")
+
+    def get_tuning(self, precision: str, n_cas: int) -> dict:
+        t = MbeTuning()
+        _check(lib().mbe_ctx_get_tuning(self._h, {"fp64": MBE_PREC_FP64, "mixed": MBE_PREC_MIXED}[precision],
+                                        int(n_cas), ctypes.byref(t)), "mbe_ctx_get_tuning")
+        return self._tuning_dict(t)
+
+    def autotune(self, h1, eri, occ, ref: Sequence[int], e_ref_corr: float, order: int, tuples: torch.Tensor,
+                 opts: Optional[Opts] = None):
+        """mbe_autotune on `tuples`: the chosen tuning (set on the context for this
+        precision and |R| + order) and the timed candidates [(tuning, ms)]."""
+        norb = h1.shape[0]
+        self._dev(tuples, torch.int32, "tuples")
+        o = (opts or Opts()).to_c()
+        best = MbeTuning()
+        recs = (MbeTuneRecord * 16)()
+        nrec = ctypes.c_int()
+        _check(lib().mbe_autotune(self._h, norb, self._p(self._dev(h1, torch.float64, "h1")),
+                                  self._p(self._dev(eri, torch.float64, "eri")),
+                                  self._p(self._dev(occ, torch.uint8, "occ")), len(ref), _i32_host(ref),
+                                  float(e_ref_corr), order, int(tuples.shape[0]), self._p(tuples), ctypes.byref(o),
+                                  ctypes.byref(best), recs, 16, ctypes.byref(nrec)), "mbe_autotune")
+        return (self._tuning_dict(best),
+                [(self._tuning_dict(recs[i].tuning), recs[i].ms) for i in range(min(nrec.value, 16))])
 
     # ---------------------------------------------------------------- helpers
     def _dev(self, t: torch.Tensor, dtype: torch.dtype, name: str) -> torch.Tensor:

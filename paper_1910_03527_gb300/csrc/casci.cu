@@ -34,7 +34,7 @@ namespace mbe {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int WARP_MAX_N = 8;
-constexpr int WARP_MAX_NDET = 416;
+constexpr int WARP_MAX_NDET = 416;  // determinants one warp holds (13 per lane); mbe_tuning's upper limit
 constexpr int WARPS_PER_BLOCK = 4;
 constexpr int CTA_THREADS = 256;
 constexpr int MAX_BUCKETS = 8;
@@ -72,6 +72,8 @@ struct BatchArgs {
     // (pstate: [flag, float32 sigma count] per tuple) for the float64 redo launch
     unsigned long long *counters2;
     int32_t *pstate;
+    // tuned launch choices (mbe_tuning): warps per warp-solver block, block-solver basis
+    int warps, block_basis;
     // adjoint (casci_rdm_batch): 0 = energies only, 1 = + 1-RDM, 2 = + 1- and 2-RDM
     int rdm;
     const double *weights;
@@ -575,63 +577,6 @@ __device__ void rdm_flush(const BatchArgs &a, const Problem &pb, const double *g
 
 // ------------------------------------------------------------------ warp solver
 
-// The tuples of the warp solver (<= 416 determinants, <= 8 orbitals) have at most
-// WARP_RMAX single-replacement entries per string (k (n - k + 1), largest at n = 8,
-// k = 7); the launch checks it.
-constexpr int WARP_RMAX = 14;
-
-// a5 for the warp solver: the element of sigma_elem with the beta list of I_b
-// decoded once into registers (pair index and column of c packed in one word,
-// signs in a bit mask), so that the gathers of one alpha entry are all
-// independent and in flight together (the loop over the list is unrolled to
-// WARP_RMAX with the tail predicated off).
-template <typename T>
-__device__ inline T sigma_elem_warp(const Problem &pb, const T *__restrict__ V, const T *__restrict__ Hs,
-                                    const T *__restrict__ c, int d)
-{
-    const int Ns = pb.Ns, P = pb.P, R = pb.R;
-    const int ia = d / Ns, ib = d - ia * Ns;
-    const T *ha = Hs + ia * pb.HSS;
-    const T *hb = Hs + ib * pb.HSS;
-    const T *crow = c + ia * Ns;
-    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    int J = 0;
-    for (; J + 1 < Ns; J += 2) {
-        a0 = fma(ha[J], c[J * Ns + ib], a0);
-        a1 = fma(hb[J], crow[J], a1);
-        a2 = fma(ha[J + 1], c[(J + 1) * Ns + ib], a2);
-        a3 = fma(hb[J + 1], crow[J + 1], a3);
-    }
-    if (J < Ns) {
-        a0 = fma(ha[J], c[J * Ns + ib], a0);
-        a1 = fma(hb[J], crow[J], a1);
-    }
-    const int32_t *tb = pb.tab + ib * pb.RS;
-    uint32_t bw[WARP_RMAX];  // (J_y << 16) | pair_y
-    uint32_t bn = 0;         // bit y: sign of entry y
-#pragma unroll
-    for (int y = 0; y < WARP_RMAX; ++y) {
-        const int e = y < R ? tb[y] : 0;
-        bw[y] = ((uint32_t)entry_J(e) << 16) | (uint32_t)entry_pair(e);
-        bn |= (uint32_t)entry_neg(e) << y;
-    }
-    const int32_t *ta = pb.tab + ia * pb.RS;
-#pragma unroll 1
-    for (int x = 0; x < R; ++x) {
-        const int ea = ta[x];
-        const T *vrow = V + entry_pair(ea) * P;
-        const T *cr = c + entry_J(ea) * Ns;
-        T s[4] = {0, 0, 0, 0};
-#pragma unroll
-        for (int y = 0; y < WARP_RMAX; ++y)
-            if (y < R)
-                s[y & 3] = fma(flip_if(vrow[bw[y] & 0xffffu], (bn >> y) & 1u), cr[bw[y] >> 16], s[y & 3]);
-        const T sx = (s[0] + s[1]) + (s[2] + s[3]);
-        if (x & 1) a1 += flip_if(sx, entry_neg(ea)); else a0 += flip_if(sx, entry_neg(ea));
-    }
-    return (a0 + a1) + (a2 + a3);
-}
-
 template <typename T, int DPL, typename TV = T>
 __device__ inline void sigma_warp(const Problem &pb, const T *V, const T *Hs, const TV *c, T *sbuf, T (&out)[DPL])
 {
@@ -647,11 +592,7 @@ __device__ inline void sigma_warp(const Problem &pb, const T *V, const T *Hs, co
 #pragma unroll 1
     for (int h = lane; h < nh; h += 32) {
         const int d = ia * Ns + ib, pd = ib * Ns + ia;
-        T v;
-        if constexpr (sizeof(T) == sizeof(TV))
-            v = (pb.sector < 0 && ia == ib) ? (T)0 : sigma_elem_warp<T>(pb, V, Hs, c, d);
-        else
-            v = (pb.sector < 0 && ia == ib) ? (T)0 : sigma_elem<T, TV>(pb, V, Hs, c, d);
+        const T v = (pb.sector < 0 && ia == ib) ? (T)0 : sigma_elem<T, TV>(pb, V, Hs, c, d);
         sbuf[d] = v;
         if (pd != d) sbuf[pd] = pb.sector > 0 ? v : -v;
         tri_advance(ia, ib, 32, Ns);
@@ -725,6 +666,9 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
     o.dnorm = 0.0;
 
     T lam = 0;
+    // The first pass (plain mode) forms H x through the same sigma call that later
+    // forms each correction's image: one call site keeps the kernel's code small.
+    bool first = !anch;
     if (!anch) {
         T s = 0;
 #pragma unroll
@@ -737,14 +681,6 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
             int d = lane + 32 * j;
             if (d < pb.N) c[d] = x[j];
         }
-        __syncwarp();
-        sigma_warp<T, DPL>(pb, V, Hs, c, sbuf, hx);
-        ++o.nsig;
-        __syncwarp();
-        T xh = 0;
-#pragma unroll
-        for (int j = 0; j < DPL; ++j) xh += x[j] * hx[j];
-        lam = warp_sum(xh);
     } else {
 #pragma unroll
         for (int j = 0; j < DPL; ++j) x[j] = hx[j] = 0;  // x = x0: A x = r0, mu = x0.r0 = 0
@@ -755,7 +691,9 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
     T best = (T)3e38;
     int stall = 0;
     T rn = 0;
-    for (int it = 0;; ++it) {
+    T xx = 1;  // |x|^2: 1 in plain mode (x normalised), |x0 + d|^2 when anchored
+    for (int it = 0;;) {
+      if (!first) {
         T rr = 0;
 #pragma unroll
         for (int j = 0; j < DPL; ++j) {
@@ -798,7 +736,6 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
             }
             t0n = sqrt(warp_sum(t0n));
         }
-        T xx = 1;
         if (anch) {
             T s = 0;
 #pragma unroll
@@ -847,10 +784,23 @@ __device__ PhaseOut davidson_warp(const Problem &pb, T (&x)[DPL], double tol, in
             int d = lane + 32 * j;
             if (d < pb.N) c[d] *= tinv;
         }
+      }
         __syncwarp();
         sigma_warp<T, DPL>(pb, V, Hs, c, sbuf, ht);
         ++o.nsig;
         __syncwarp();
+        if (first) {
+            T xh = 0;
+#pragma unroll
+            for (int j = 0; j < DPL; ++j) {
+                hx[j] = ht[j];
+                xh += x[j] * ht[j];
+            }
+            lam = warp_sum(xh);
+            first = false;
+            continue;
+        }
+        ++it;
         // G = [x p t]^T A [x p t]; a coupling x.(A v) is formed as v.r0 + d.(A v)
         T g00 = 0, g01 = 0, g02 = 0, g11 = 0, g12 = 0, g22 = 0;
 #pragma unroll
@@ -1924,7 +1874,7 @@ __device__ inline void sigma_block(const Problem &pb, const T *Vi, const T *Hs, 
 template <typename T>
 __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *x, T *hx, T *tx, char *smem,
                                    const BlockSmem &S, double tol, int min_iter, int max_iter, int steer,
-                                   double shift = 0.0, bool anch = false)
+                                   double shift = 0.0, bool anch = false, int mmax = MMAX)
 {
     const int tid = threadIdx.x, nt = blockDim.x, N = pb.N;
     const T *Vi = sizeof(T) == 8 ? (const T *)pb.V64 : (const T *)pb.V32;
@@ -1971,7 +1921,7 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
         __syncthreads();
         theta = misc[0];
         const T th = (T)theta;
-        T *tdst = (m < MMAX) ? V + (size_t)m * ld : tx;
+        T *tdst = (m < mmax) ? V + (size_t)m * ld : tx;
         v[0] = 0;
         v[1] = 0;
         for (int d = tid; d < N; d += nt) {
@@ -2012,13 +1962,13 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
                 break;
             }
         }
-        if (m == MMAX && anch) {
+        if (m == mmax && anch) {
             // Thick restart that keeps the anchor: V[0] = x0, W[0] = r0 stay; V[1], V[2]
             // become the corrections of the two lowest Ritz vectors (both orthogonal
             // to x0), orthonormalised.
             for (int d = tid; d < N; d += nt) {
                 T u1 = 0, w1 = 0, u2 = 0, w2 = 0;
-                for (int i = 1; i < MMAX; ++i) {
+                for (int i = 1; i < mmax; ++i) {
                     const T vi = V[(size_t)i * ld + d], wi = W[(size_t)i * ld + d];
                     u1 += (T)ys[i] * vi;
                     w1 += (T)ys[i] * wi;
@@ -2084,12 +2034,12 @@ __device__ PhaseOut davidson_block(const Problem &pb, T *V, T *W, size_t ld, T *
                 }
             }
             m = mnew;
-        } else if (m == MMAX) {
+        } else if (m == mmax) {
             // Thick restart on the two lowest Ritz vectors of the current basis
             // (orthogonal by construction, so W stays consistent with H V).
             for (int d = tid; d < N; d += nt) {
                 T x2 = 0, hx2 = 0;
-                for (int i = 0; i < MMAX; ++i) {
+                for (int i = 0; i < mmax; ++i) {
                     T yi = (T)y2s[i];
                     x2 += yi * V[(size_t)i * ld + d];
                     hx2 += yi * W[(size_t)i * ld + d];
@@ -2357,7 +2307,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
                     const double tl = (sector == 0 || pass == 1) ? a.tol_switch : SECTOR_TOL;
                     o32 = davidson_block<float>(pb, (float *)(slot + L.off_V), (float *)(slot + L.off_W), L.vec / 4,
                                                 x32, (float *)(slot + L.off_hx), (float *)(slot + L.off_t), smem, S,
-                                                tl, 0, a.max_iter, BLOCK_STALL);
+                                                tl, 0, a.max_iter, BLOCK_STALL, 0.0, false, a.block_basis);
                     n32 += o32.nsig;
                     if (sector == 1)
                         lose = o32.status == MBE_STATUS_NONFINITE ||
@@ -2395,7 +2345,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
                         __syncthreads();
                         PhaseOut o = davidson_block<float>(pb, V0, W0, L.vec / 4, x32, (float *)(slot + L.off_hx),
                                                            (float *)(slot + L.off_t), smem, S, a.tol, a.min_fp64,
-                                                           a.max_iter, BLOCK_ANCHOR_STALL, th, true);
+                                                           a.max_iter, BLOCK_ANCHOR_STALL, th, true, a.block_basis);
                         n32 += o.nsig;
                         lam_s = th + o.lambda;
                         bad = o.status == MBE_STATUS_NONFINITE;
@@ -2430,7 +2380,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
                 PhaseOut o1 = davidson_block<double>(pb, (double *)(slot + L.off_V), (double *)(slot + L.off_W),
                                                      L.vec / 8, x64, (double *)(slot + L.off_hx),
                                                      (double *)(slot + L.off_t), smem, S, SECTOR_TOL, 0,
-                                                     a.max_iter, BLOCK_STALL);
+                                                     a.max_iter, BLOCK_STALL, 0.0, false, a.block_basis);
                 n64 += o1.nsig;
                 lose = o1.status == MBE_STATUS_NONFINITE || sector_loses(o1.lambda, o1.rnorm, lam, 0.0);
             }
@@ -2438,7 +2388,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
                 PhaseOut o64 = davidson_block<double>(pb, (double *)(slot + L.off_V), (double *)(slot + L.off_W),
                                                       L.vec / 8, x64, (double *)(slot + L.off_hx),
                                                       (double *)(slot + L.off_t), smem, S, a.tol,
-                                                      mixed ? a.min_fp64 : 0, a.max_iter, 0);
+                                                      mixed ? a.min_fp64 : 0, a.max_iter, 0, 0.0, false, a.block_basis);
                 n64 += o64.nsig;
                 if (sector == 0) {
                     lam = o64.lambda;
@@ -2578,15 +2528,14 @@ struct Bucket {
 template <int DPL>
 static int launch_warp_mixed(mbe_ctx *ctx, const BatchArgs &a, int b, const MixLayout &L)
 {
-    const size_t smem = (size_t)L.bytes * WARPS_PER_BLOCK;
+    const size_t smem = (size_t)L.bytes * a.warps;
     MBE_CHECK(smem <= ctx->smem_optin, MBE_EUNSUPPORTED, "casci_batch: mixed warp solver needs %zu B shared memory",
               smem);
     MBE_CU(cudaFuncSetAttribute(k_casci_warp_mixed<DPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_casci_warp_mixed<DPL>, WARPS_PER_BLOCK * 32,
-                                                         smem));
+    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_casci_warp_mixed<DPL>, a.warps * 32, smem));
     if (per_sm < 1) per_sm = 1;
-    k_casci_warp_mixed<DPL><<<ctx->sm_count * per_sm, WARPS_PER_BLOCK * 32, smem, ctx->stream>>>(a, b, L);
+    k_casci_warp_mixed<DPL><<<ctx->sm_count * per_sm, a.warps * 32, smem, ctx->stream>>>(a, b, L);
     MBE_CU(cudaGetLastError());
     ++ctx->launches;
     return MBE_OK;
@@ -2597,10 +2546,9 @@ static int launch_warp_mode(mbe_ctx *ctx, const BatchArgs &a, int b, const WarpL
 {
     MBE_CU(cudaFuncSetAttribute(k_casci_warp<DPL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_casci_warp<DPL, MODE>, WARPS_PER_BLOCK * 32,
-                                                         smem));
+    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_casci_warp<DPL, MODE>, a.warps * 32, smem));
     if (per_sm < 1) per_sm = 1;
-    k_casci_warp<DPL, MODE><<<ctx->sm_count * per_sm, WARPS_PER_BLOCK * 32, smem, ctx->stream>>>(a, b, L);
+    k_casci_warp<DPL, MODE><<<ctx->sm_count * per_sm, a.warps * 32, smem, ctx->stream>>>(a, b, L);
     MBE_CU(cudaGetLastError());
     ++ctx->launches;
     return MBE_OK;
@@ -2612,7 +2560,7 @@ template <int DPL>
 static int launch_warp(mbe_ctx *ctx, const BatchArgs &a, int b, const Bucket &bk)
 {
     WarpLayout L = warp_layout(a.n, bk.max_ns, bk.max_r, bk.max_n, a.rdm != 0);
-    size_t smem = (size_t)L.bytes * WARPS_PER_BLOCK;
+    size_t smem = (size_t)L.bytes * a.warps;
     MBE_CHECK(smem <= ctx->smem_optin, MBE_EUNSUPPORTED, "casci_batch: warp solver needs %zu B shared memory",
               smem);
     TimedLaunch tl(ctx, a.order, 0, DPL);
@@ -2701,6 +2649,9 @@ static int run_casci(mbe_ctx *ctx, int norb, const double *h1, const double *eri
     a.max_iter = o.max_iter;
     a.min_fp64 = o.fp64_final_iters;
     a.even_only = o.sectors == MBE_SECTORS_EVEN ? 1 : 0;
+    const mbe_tuning tu = ctx->tune[o.precision == MBE_PREC_MIXED ? 1 : 0][n];
+    a.warps = tu.warp_warps;
+    a.block_basis = tu.block_basis;
     a.eps = eps_out;
     a.status = status_out;
     a.iters = iters_out;
@@ -2721,7 +2672,7 @@ static int run_casci(mbe_ctx *ctx, int norb, const double *h1, const double *eri
         a.cls[k].r = st->r;
         int64_t N = st->ns * st->ns;
         int b;
-        if (n <= WARP_MAX_N && N <= WARP_MAX_NDET && st->r <= WARP_RMAX && rdm != 2) {
+        if (n <= WARP_MAX_N && N <= tu.warp_max_ndet && rdm != 2) {
             int di = 0;
             while (DPL_SET[di] * 32 < N) ++di;
             if (warp_bucket_of_dpl[di] < 0) {
@@ -2840,6 +2791,84 @@ extern "C" int casci_batch(mbe_ctx *ctx, int norb, const double *h1, const doubl
 {
     return run_casci(ctx, norb, h1, eri, occ, n_ref, ref_orbs, e_ref_corr, order, n_tuples, tuples, opts, eps_out,
                      status_out, iters_out, 0, nullptr, nullptr, nullptr);
+}
+
+// Autotuner of the launch choices (see include/mbe.h): each tuning field in turn,
+// candidates timed on the caller's tuples with CUDA events (best of two calls
+// after a warm-up call), the fastest kept.
+extern "C" int mbe_autotune(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,
+                            int n_ref, const int32_t *ref_orbs, double e_ref_corr, int order, int64_t n_tuples,
+                            const int32_t *tuples, const mbe_opts *opts, mbe_tuning *best, mbe_tune_record *records,
+                            int max_records, int *n_records)
+{
+    MBE_CHECK(ctx && best && n_records && (max_records == 0 || records), MBE_EINVAL, "mbe_autotune: NULL argument");
+    MBE_CHECK(n_tuples >= 1, MBE_EINVAL, "mbe_autotune: no tuples");
+    mbe_opts o;
+    if (opts) o = *opts; else mbe_default_opts(&o);
+    MBE_CHECK(o.precision == MBE_PREC_FP64 || o.precision == MBE_PREC_MIXED, MBE_EINVAL,
+              "mbe_autotune: unknown precision %d", o.precision);
+    const int n = n_ref + order;
+    MBE_CHECK(n >= 1 && n <= MBE_MAX_CAS, MBE_EUNSUPPORTED, "mbe_autotune: |R| + order = %d", n);
+    MBE_CU(cudaSetDevice(ctx->device));
+    const int p = o.precision == MBE_PREC_MIXED ? 1 : 0;
+    double *eps = nullptr;
+    int32_t *st = nullptr;
+    MBE_CU(cudaMallocAsync((void **)&eps, (size_t)n_tuples * 8, ctx->stream));
+    MBE_CU(cudaMallocAsync((void **)&st, (size_t)n_tuples * 4, ctx->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MBE_CU(cudaEventCreate(&e0));
+    MBE_CU(cudaEventCreate(&e1));
+    const bool timing = ctx->timing;
+    ctx->timing = false;
+    int nrec = 0, rc = MBE_OK;
+    auto time_one = [&](const mbe_tuning &t, float *ms) -> int {
+        ctx->tune[p][n] = t;
+        float bestms = 3e38f;
+        for (int rep = 0; rep < 3; ++rep) {
+            if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) return MBE_ECUDA;
+            int r = run_casci(ctx, norb, h1, eri, occ, n_ref, ref_orbs, e_ref_corr, order, n_tuples, tuples, &o,
+                              eps, st, nullptr, 0, nullptr, nullptr, nullptr);
+            if (r) return r;
+            MBE_CU(cudaEventRecord(e1, ctx->stream));
+            MBE_CU(cudaEventSynchronize(e1));
+            float t_ms = 0.f;
+            MBE_CU(cudaEventElapsedTime(&t_ms, e0, e1));
+            if (rep > 0) bestms = std::min(bestms, t_ms);  // call 0 warms up
+        }
+        *ms = bestms;
+        if (nrec < max_records) records[nrec] = mbe_tune_record{t, bestms};
+        ++nrec;
+        return MBE_OK;
+    };
+    mbe_tuning cur = ctx->tune[p][n];
+    const int warps_c[] = {2, 4}, ndet_c[] = {100, 225, 416}, basis_c[] = {12, 16, 20};
+    for (int field = 0; field < 3 && rc == MBE_OK; ++field) {
+        const int *cand = field == 0 ? warps_c : field == 1 ? ndet_c : basis_c;
+        const int nc = field == 0 ? 2 : 3;
+        float bms = 3e38f;
+        mbe_tuning bt = cur;
+        for (int i = 0; i < nc && rc == MBE_OK; ++i) {
+            mbe_tuning t = cur;
+            (field == 0 ? t.warp_warps : field == 1 ? t.warp_max_ndet : t.block_basis) = cand[i];
+            float ms = 0.f;
+            rc = time_one(t, &ms);
+            if (rc == MBE_OK && ms < bms) {
+                bms = ms;
+                bt = t;
+            }
+        }
+        cur = bt;
+    }
+    ctx->tune[p][n] = cur;
+    ctx->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(eps, ctx->stream);
+    cudaFreeAsync(st, ctx->stream);
+    if (rc) return rc;
+    *best = cur;
+    *n_records = nrec;
+    return MBE_OK;
 }
 
 extern "C" int casci_rdm_batch(mbe_ctx *ctx, int norb, const double *h1, const double *eri, const uint8_t *occ,

@@ -96,6 +96,9 @@ struct mbe_ctx {
     size_t ws_size = 0;
     mbe::StringTable tables[MBE_MAX_STRING_ORB + 1][MBE_MAX_STRING_ORB + 1];
     int *dev_err = nullptr;  // device flag set by a kernel whose bounded wait ran out
+    // launch choices of casci_batch per precision (0 float64, 1 mixed) and active-space
+    // size |R| + order (mbe_ctx_set_tuning, mbe_autotune)
+    mbe_tuning tune[2][MBE_MAX_CAS + 1];
     int64_t launches = 0;  // kernels launched by this context
     bool timing = false;
     struct Pending {

@@ -155,6 +155,8 @@ int mbe_ctx_create(mbe_ctx **ctx, int device, void *cuda_stream)
     }
     c->sm_count = prop.multiProcessorCount;
     c->smem_optin = prop.sharedMemPerBlockOptin;
+    for (auto &row : c->tune)
+        for (auto &t : row) t = mbe_tuning{416, 4, 20};
     e = cudaMalloc(&c->dev_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->dev_err, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -163,6 +165,32 @@ int mbe_ctx_create(mbe_ctx **ctx, int device, void *cuda_stream)
         return cuda_fail(e, "mbe_ctx_create: error flag", __FILE__, __LINE__);
     }
     *ctx = c;
+    return MBE_OK;
+}
+
+int mbe_ctx_set_tuning(mbe_ctx *ctx, int precision, int n_cas, const mbe_tuning *t)
+{
+    MBE_CHECK(ctx && t, MBE_EINVAL, "mbe_ctx_set_tuning: NULL argument");
+    MBE_CHECK(precision == MBE_PREC_FP64 || precision == MBE_PREC_MIXED, MBE_EINVAL,
+              "mbe_ctx_set_tuning: precision %d", precision);
+    MBE_CHECK(n_cas >= 0 && n_cas <= MBE_MAX_CAS, MBE_EINVAL, "mbe_ctx_set_tuning: n_cas %d", n_cas);
+    MBE_CHECK(t->warp_max_ndet >= 1 && t->warp_max_ndet <= 416 && t->warp_warps >= 1 && t->warp_warps <= 4 &&
+                  t->block_basis >= 4 && t->block_basis <= 20,
+              MBE_EINVAL, "mbe_ctx_set_tuning: values out of range (%d, %d, %d)", t->warp_max_ndet, t->warp_warps,
+              t->block_basis);
+    const int p = precision == MBE_PREC_MIXED ? 1 : 0;
+    for (int n = 0; n <= MBE_MAX_CAS; ++n)
+        if (n_cas == 0 || n == n_cas) ctx->tune[p][n] = *t;
+    return MBE_OK;
+}
+
+int mbe_ctx_get_tuning(const mbe_ctx *ctx, int precision, int n_cas, mbe_tuning *t)
+{
+    MBE_CHECK(ctx && t, MBE_EINVAL, "mbe_ctx_get_tuning: NULL argument");
+    MBE_CHECK(precision == MBE_PREC_FP64 || precision == MBE_PREC_MIXED, MBE_EINVAL,
+              "mbe_ctx_get_tuning: precision %d", precision);
+    MBE_CHECK(n_cas >= 0 && n_cas <= MBE_MAX_CAS, MBE_EINVAL, "mbe_ctx_get_tuning: n_cas %d", n_cas);
+    *t = ctx->tune[precision == MBE_PREC_MIXED ? 1 : 0][n_cas];
     return MBE_OK;
 }
 

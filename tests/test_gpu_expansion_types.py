@@ -18,6 +18,10 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
+# a tuple energy is valid with status OK (0) or DEGENERATE (4: the two spin-flip
+# sectors' lowest eigenvalues coincide; the energy is unique, the state is not)
+VALID = (0, 4)
+
 from oracle import fci, mbe as omb  # noqa: E402
 from workloads import random_system  # noqa: E402
 
@@ -76,7 +80,7 @@ def test_expansion_type_matches_oracle(eng, ctx, system, case, prec):
     for i, n in enumerate(orders):
         tk = [tuple(int(x) for x in r) for r in got["tuples"][i].cpu().numpy()]
         assert tk == omb.tuples(exp, ref, occ, n, True)
-        assert int((got["status"][i] != 0).sum()) == 0
+        assert np.isin(got["status"][i].cpu().numpy(), VALID).all()
         eps = got["eps"][i].cpu().numpy()
         assert np.abs(eps - np.array([want["eps"][n][t] for t in tk])).max() <= tol, n
         inc = got["inc"][i].cpu().numpy()
@@ -130,7 +134,7 @@ def test_routed_tuples_match_oracle(eng, ctx, system, case, large_ndet, prec):
     n_routed = 0
     for i, n in enumerate(orders):
         tk = [tuple(int(x) for x in r) for r in got["tuples"][i].cpu().numpy()]
-        assert int((got["status"][i] != 0).sum()) == 0
+        assert np.isin(got["status"][i].cpu().numpy(), VALID).all()
         assert int((got["iters"][i] <= 0).sum()) == 0 or n == 1
         eps = got["eps"][i].cpu().numpy()
         assert np.abs(eps - np.array([want["eps"][n][t] for t in tk])).max() <= tol, n
@@ -171,7 +175,7 @@ def test_active_spaces_beyond_the_batched_limit(eng, ctx, prec):
     tol = TOL[prec]
     assert abs(got["e_ref_corr"] - e_ref) <= tol
     for i, n in enumerate([1, 2]):
-        assert int((got["status"][i] != 0).sum()) == 0
+        assert np.isin(got["status"][i].cpu().numpy(), VALID).all()
         tk = [tuple(int(x) for x in r) for r in got["tuples"][i].cpu().numpy()]
         eps = got["eps"][i].cpu().numpy()
         assert np.abs(eps - np.array([want[t] for t in tk])).max() <= tol

@@ -24,6 +24,10 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
+# a tuple energy is valid with status OK (0) or DEGENERATE (4: the two spin-flip
+# sectors' lowest eigenvalues coincide; the energy is unique, the state is not)
+VALID = (0, 4)
+
 from oracle_full import run_mbe_parallel  # noqa: E402
 from workloads import workload  # noqa: E402
 
@@ -87,7 +91,7 @@ def test_every_increment_and_total(eng, ctx, oracle_runs, name, prec):
         if not tup:
             continue
         st = out["status"][i].cpu().numpy()
-        assert (st == 0).all(), (name, n, np.bincount(st))
+        assert np.isin(st, VALID).all(), (name, n, np.bincount(st))
         eps = out["eps"][i].cpu().numpy()
         inc = out["inc"][i].cpu().numpy()
         want_e = np.array([ref["eps"][n][t] for t in tup])

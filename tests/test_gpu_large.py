@@ -16,6 +16,10 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
+# a tuple energy is valid with status OK (0) or DEGENERATE (4: the two spin-flip
+# sectors' lowest eigenvalues coincide; the energy is unique, the state is not)
+VALID = (0, 4)
+
 from oracle import fci, mbe as omb  # noqa: E402
 from workloads import hubbard_ring_momentum, random_system, synthetic_molecule  # noqa: E402
 
@@ -103,7 +107,7 @@ def test_large_sigma_16_orbitals_sampled_rows(eng, ctx, molecule):
 def test_casci_solve_hubbard8_full_space(eng, ctx, prec):
     h1, eri, occ, _ = hubbard_ring_momentum(8, 1.0, 4.0)
     res = ctx.casci_solve(dev(h1), dev(eri), dev(occ), list(range(8)), eng.Opts(precision=prec, tol=1e-7))
-    assert res["status"] == 0
+    assert res["status"] in VALID
     exact = fci.lowest_eigenvalue(h1, eri, 4, 4)
     assert abs(res["lam"] - exact) < 1e-9
     assert abs(res["eps"] - (exact - omb.phi_energy(h1, eri, occ))) < 1e-9
@@ -116,7 +120,7 @@ def test_casci_solve_molecule_12o_row_sampled_residual(eng, ctx, molecule):
     A = list(range(2, 14))  # (12e,12o): 853,776 determinants
     res = ctx.casci_solve(dev(h1), dev(eri), dev(occ), A, eng.Opts(precision="mixed", tol=1e-6, max_iter=3000),
                           want_vector=True)
-    assert res["status"] == 0 and res["rnorm"] <= 1e-6, res
+    assert res["status"] in VALID and res["rnorm"] <= 1e-6, res
     c = res["c"].cpu().numpy()
     assert abs(np.linalg.norm(c) - 1.0) < 1e-10
     k = omb.n_active_electrons(occ, A)

@@ -21,6 +21,10 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
+# a tuple energy is valid with status OK (0) or DEGENERATE (4: the two spin-flip
+# sectors' lowest eigenvalues coincide; the energy is unique, the state is not)
+VALID = (0, 4)
+
 from workloads import workload  # noqa: E402
 
 TOL = {"fp64": 1e-9, "mixed": 1e-8}
@@ -69,6 +73,6 @@ def test_block_solver_tuple_energies(eng, ctx, sample, order, prec, even_only):
     eps, st, it = ctx.casci_batch(h1, eri, occ, w.ref, sample["e_ref_corr"], order, tup, opts)
     eps, st = eps.cpu().numpy(), st.cpu().numpy()
     want = np.array([r["eps_even" if even_only else "eps"] for r in rows])
-    assert (st == 0).all(), st
+    assert np.isin(st, VALID).all(), st
     err = np.abs(eps - want)
     assert err.max() <= TOL[prec], [(r["tuple"], float(e)) for r, e in zip(rows, err) if e > TOL[prec]]

@@ -16,6 +16,10 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
+# a tuple energy is valid with status OK (0) or DEGENERATE (4: the two spin-flip
+# sectors' lowest eigenvalues coincide; the energy is unique, the state is not)
+VALID = (0, 4)
+
 from fock_space import annihilators  # noqa: E402
 from oracle import fci, mbe as omb  # noqa: E402
 from workloads import (hubbard_ring_momentum, random_system, workload)  # noqa: E402
@@ -145,7 +149,7 @@ def test_full_mbe_hubbard8(eng, ctx, prec):
     for i, n in enumerate(w.orders):
         tup = [tuple(r) for r in out["tuples"][i].cpu().tolist()]
         assert tup == list(ref["eps"][n].keys())
-        assert (out["status"][i].cpu().numpy() == 0).all()
+        assert np.isin(out["status"][i].cpu().numpy(), VALID).all()
         eps = out["eps"][i].cpu().numpy()
         want = np.array([ref["eps"][n][t] for t in tup])
         assert np.abs(eps - want).max() <= tol, (n, np.abs(eps - want).max())
@@ -215,7 +219,7 @@ def test_hubbard22_full_size_sampled(eng, ctx, prec):
     torch.cuda.synchronize()
     for i, n in enumerate(w.orders):
         st = out["status"][i].cpu().numpy()
-        assert (st == 0).all(), (n, np.bincount(st))
+        assert np.isin(st, VALID).all(), (n, np.bincount(st))
     tuples = {n: out["tuples"][i] for i, n in enumerate(w.orders)}
     eps = {n: out["eps"][i] for i, n in enumerate(w.orders)}
     inc = {n: out["inc"][i] for i, n in enumerate(w.orders)}
@@ -236,7 +240,7 @@ def test_hubbard46_sampled(eng, ctx, prec):
     eps = {n: out["eps"][i] for i, n in enumerate(w.orders)}
     inc = {n: out["inc"][i] for i, n in enumerate(w.orders)}
     for i, n in enumerate(w.orders):
-        assert (out["status"][i].cpu().numpy() == 0).all()
+        assert np.isin(out["status"][i].cpu().numpy(), VALID).all()
     rng = np.random.default_rng(46)
     for n, ns in ((2, 20), (3, 15), (4, 10)):
         _sampled_increments(w, tuples, eps, inc, n, rng, ns, prec)
@@ -252,7 +256,7 @@ def test_molecule40_orders_1_2_sampled(eng, ctx, prec):
     eps = {n: out["eps"][i] for i, n in enumerate([1, 2])}
     inc = {n: out["inc"][i] for i, n in enumerate([1, 2])}
     for i in range(2):
-        assert (out["status"][i].cpu().numpy() == 0).all()
+        assert np.isin(out["status"][i].cpu().numpy(), VALID).all()
     rng = np.random.default_rng(40)
     _sampled_increments(w, tuples, eps, inc, 1, rng, 8, prec)
     _sampled_increments(w, tuples, eps, inc, 2, rng, 4, prec)

@@ -23,6 +23,10 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
+# a tuple energy is valid with status OK (0) or DEGENERATE (4: the two spin-flip
+# sectors' lowest eigenvalues coincide; the energy is unique, the state is not)
+VALID = (0, 4)
+
 from oracle import mbe as omb  # noqa: E402
 from workloads import random_system  # noqa: E402
 
@@ -152,7 +156,7 @@ def test_screened_expansion_matches_oracle(eng, ctx, case, prec):
         gi = got["inc"][k - 1].cpu().numpy()
         wi = np.array([want["inc"][t] for t in tk])
         assert np.abs(gi - wi).max() <= tol
-        assert int((got["status"][k - 1] != 0).sum()) == 0
+        assert np.isin(got["status"][k - 1].cpu().numpy(), VALID).all()
     assert abs(float(got["e_total"].item()) - want["e_tot"]) <= 10 * tol
 
 

@@ -18,6 +18,10 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
+# a tuple energy is valid with status OK (0) or DEGENERATE (4: the two spin-flip
+# sectors' lowest eigenvalues coincide; the energy is unique, the state is not)
+VALID = (0, 4)
+
 from oracle import adjoint, fci, mbe as omb  # noqa: E402
 from workloads import random_system  # noqa: E402
 
@@ -75,7 +79,7 @@ def test_tuple_energies_all_orders(eng, ctx, system, prec):
         want = np.array([omb.tuple_energy(h1, eri, occ, [], t, e_phi, 0.0) for t in tups])
         eps, status, _ = ctx.casci_batch(dev(h1), dev(eri), dev(occ), [], 0.0, n,
                                          dev(np.array(tups, dtype=np.int32)), eng.Opts(precision=prec))
-        assert int((status != 0).sum()) == 0
+        assert np.isin(status.cpu().numpy(), VALID).all()
         assert np.abs(eps.cpu().numpy() - want).max() <= tol, n
 
 
@@ -100,7 +104,7 @@ def test_large_solver_finds_the_odd_ground_state(eng, ctx, system, prec):
     k = omb.n_active_electrons(occ, ODD)
     _, he, ea = omb.frozen_core(h1, eri, occ, list(ODD))
     res = ctx.casci_solve(dev(h1), dev(eri), dev(occ), list(ODD), eng.Opts(precision=prec, tol=1e-7))
-    assert res["status"] == 0
+    assert res["status"] in VALID
     assert abs(res["lam"] - fci.lowest_eigenvalue(he, ea, k, k)) < 1e-9
 
 
@@ -118,12 +122,12 @@ def test_even_sector_targeting(eng, ctx, system, prec):
         want = np.array([omb.tuple_energy(h1, eri, occ, [], t, e_phi, 0.0, even_only=True) for t in tups])
         eps, status, _ = ctx.casci_batch(dev(h1), dev(eri), dev(occ), [], 0.0, n,
                                          dev(np.array(tups, dtype=np.int32)), eng.Opts(precision=prec, even_only=True))
-        assert int((status != 0).sum()) == 0
+        assert np.isin(status.cpu().numpy(), VALID).all()
         assert np.abs(eps.cpu().numpy() - want).max() <= tol, n
     k = omb.n_active_electrons(occ, ODD)
     _, he, ea = omb.frozen_core(h1, eri, occ, list(ODD))
     res = ctx.casci_solve(dev(h1), dev(eri), dev(occ), list(ODD), eng.Opts(precision=prec, tol=1e-7, even_only=True))
-    assert res["status"] == 0
+    assert res["status"] in VALID
     assert abs(res["lam"] - fci.lowest_eigenvalue_even(he, ea, k)) < 1e-9
 
 
