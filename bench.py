@@ -572,7 +572,8 @@ def run_ncu_case(args):
 def run_large(args):
     """Single large CASCI on the synthetic 40-orbital molecule: one float64 and one
     float32 sigma at (12e,12o), (14e,14o), (16e,16o), timed with CUDA events inside
-    the library, and a mixed-precision Davidson solve at (12e,12o)."""
+    the library, and Davidson solves (mixed and float64, residual 1e-8) of the
+    --solve-sizes active spaces."""
     import numpy as np
     import torch
 
@@ -616,16 +617,17 @@ def run_large(args):
         out["sigma"][f"{n}o"] = entry
         del c
         torch.cuda.empty_cache()
-    solves = {}
-    for prec in (() if args.no_solve else ("mixed", "fp64")):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        res = ctx.casci_solve(th1, teri, tocc, actives[12], eng.Opts(precision=prec, tol=1e-8, max_iter=3000))
-        torch.cuda.synchronize()
-        solves[prec] = dict(res, seconds=time.perf_counter() - t0)
-    out["solve_12o"] = solves
-    if solves:
-        out["solve_12o"]["abs_diff_lambda"] = abs(solves["mixed"]["lam"] - solves["fp64"]["lam"])
+    for n in ([] if args.no_solve else args.solve_sizes):
+        solves = {}
+        for prec in ("mixed", "fp64"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = ctx.casci_solve(th1, teri, tocc, actives[n], eng.Opts(precision=prec, tol=1e-8, max_iter=3000))
+            torch.cuda.synchronize()
+            solves[prec] = dict(res, seconds=time.perf_counter() - t0)
+        solves["abs_diff_lambda"] = abs(solves["mixed"]["lam"] - solves["fp64"]["lam"])
+        solves["tol"] = 1e-8
+        out[f"solve_{n}o"] = solves
     print(json.dumps(out))
     ctx.close()
 
@@ -862,7 +864,9 @@ def main():
     ap.add_argument("--large", action="store_true",
                     help="single large CASCI: sigma throughput at 12/14/16 orbitals and a 12-orbital solve")
     ap.add_argument("--large-sizes", type=int, nargs="+", default=[12, 14, 16])
-    ap.add_argument("--no-solve", action="store_true", help="--large: skip the 12-orbital Davidson solves")
+    ap.add_argument("--no-solve", action="store_true", help="--large: skip the Davidson solves")
+    ap.add_argument("--solve-sizes", type=int, nargs="+", default=[12], choices=[12, 14, 16],
+                    help="--large: active spaces solved in mixed and float64 precision (residual 1e-8)")
     ap.add_argument("--screened", action="store_true",
                     help="screened expansion (Eq. 4) on a Hubbard ring: tuples per order and solves/s")
     ap.add_argument("--screened-workload", default="hubbard22",

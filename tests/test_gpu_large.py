@@ -129,3 +129,24 @@ def test_casci_solve_molecule_12o_row_sampled_residual(eng, ctx, molecule):
     hc = fci.sigma_rows(h_eff, eri_a, k, k, c, rows)
     # the sampled components of H c - lambda c are bounded by the residual norm
     assert np.abs(hc - res["lam"] * c[rows]).max() <= 1e-6
+
+
+def test_casci_solve_molecule_14o_row_sampled_residual(eng, ctx, molecule):
+    """The largest CASCI of the paper's size class, (14e,14o) = 11,778,624
+    determinants, solved in mixed precision (float32 sigma on the tensor cores,
+    float64 anchors); 100 sampled rows of H c - lambda c from the oracle's
+    Slater-Condon rows bound the GPU vector's eigen-residual."""
+    h1, eri, occ = molecule
+    A = list(range(1, 15))
+    res = ctx.casci_solve(dev(h1), dev(eri), dev(occ), A, eng.Opts(precision="mixed", tol=1e-7, max_iter=3000),
+                          want_vector=True)
+    assert res["status"] in VALID and res["rnorm"] <= 1e-7, res
+    assert res["n64"] >= 1 and res["n32"] > res["n64"]
+    c = res["c"].cpu().numpy()
+    assert len(c) == 11_778_624
+    assert abs(np.linalg.norm(c) - 1.0) < 1e-10
+    k = omb.n_active_electrons(occ, A)
+    _, h_eff, eri_a = omb.frozen_core(h1, eri, occ, A)
+    rows = np.random.default_rng(14).choice(len(c), size=100, replace=False)
+    hc = fci.sigma_rows(h_eff, eri_a, k, k, c, rows)
+    assert np.abs(hc - res["lam"] * c[rows]).max() <= 1e-7
