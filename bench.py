@@ -169,7 +169,7 @@ def dist_env():
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("casci.cu", "common.cuh"):
+    for f in ("casci_dev.cuh", "casci_warp.cu", "casci_mixed.cu", "casci.cu", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1910_03527_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

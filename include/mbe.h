@@ -69,15 +69,17 @@ extern "C" {
 /* Precision modes of casci_batch. */
 #define MBE_PREC_FP64 0  /* every sigma and every Davidson step in float64             */
 #define MBE_PREC_MIXED 1 /* float32 sigma and Davidson until the residual reaches
-                            tol_switch; then a float64 refinement: tuple solvers of up
-                            to 416 determinants form one float64 sigma of the float32
-                            Ritz vector x0 (the anchor: theta0 = Rayleigh quotient,
-                            r0 = H x0 - theta0 x0) and continue the Davidson in
-                            float32 on H - theta0 from x0 (at least fp64_final_iters
-                            iterations, re-anchoring if it stalls), so that the
-                            energy theta0 + mu keeps float64 accuracy; the other
-                            solvers run at least fp64_final_iters float64 Davidson
-                            iterations                                               */
+                            tol_switch; then an anchored refinement in every solver
+                            (warp, block and single large CAS): one float64 sigma of
+                            the float32 Ritz vector x0 (the anchor: theta0 = its
+                            Rayleigh quotient, r0 = H x0 - theta0 x0), then the
+                            Davidson continues in float32 on H - theta0 from x0 (at
+                            least fp64_final_iters iterations), so that the energy
+                            theta0 + mu keeps float64 accuracy.  A refinement is
+                            accepted when its residual is <= tol and its correction
+                            |d| <= 3e-4; otherwise x0 + d becomes the next anchor.
+                            A tuple that does not converge within the anchor limit
+                            (3 warp, 8 block, 8 large) is solved again in float64.   */
 
 typedef struct mbe_ctx mbe_ctx;
 
