@@ -79,7 +79,7 @@ extern "C" {
                             accepted when its residual is <= tol and its correction
                             |d| <= 3e-4; otherwise x0 + d becomes the next anchor.
                             A tuple that does not converge within the anchor limit
-                            (3 warp, 8 block, 8 large) is solved again in float64.   */
+                            (6 warp, 8 block, 8 large) is solved again in float64.   */
 
 typedef struct mbe_ctx mbe_ctx;
 

@@ -1206,7 +1206,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
 // data of the anchor sigma (V, Hs) are kept as packed lower triangles, so that
 // a warp's shared memory stays near that of a float32-only solver.
 
-constexpr int MIX_ANCHORS = 3;
+constexpr int MIX_ANCHORS = 6;
 
 __host__ __device__ inline int tri_index(int a, int b)
 {

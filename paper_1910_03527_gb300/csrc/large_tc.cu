@@ -15,14 +15,22 @@
 // K step ("3xTF32"), which keeps float32-class accuracy (the dropped lo*lo term
 // is about 2^-22 of each product).
 //
-// Data path per CTA (persistent over Ia, one CTA per SM):
+// Data path per CTA (persistent over Ia, one CTA per SM, 16 warps):
 //   * the B operand (N pairs x K list entries, signed V columns) is built once per
-//     Ia in shared memory, hi and lo;
-//   * per tile of 128 beta strings: the A operand (128 x K, the gathered rows of c)
-//     is written to shared memory, one thread issues the 3 x K/8 tcgen05.mma into
-//     a TMEM accumulator and commits them to an mbarrier; after the wait, the warps
-//     copy the accumulator (tcgen05.ld) over the A operand, and each beta string
-//     scatters through its own list into a shared-memory sigma row (shared atomics);
+//     Ia in shared memory, hi and lo, by the whole CTA;
+//   * the tiles of 128 beta strings are shared out to G groups of 16/G warps that
+//     run independently (named barriers), each with its own A operand, TMEM
+//     accumulator and mbarrier: with G = 2 one group gathers its next tile while
+//     the other waits for its MMAs or scatters, so the gather latency, the tensor
+//     pipe and the shared-memory scatter overlap.  G = 2 where two A operands fit
+//     in shared memory (up to 14 orbitals), else G = 1;
+//   * per tile: the A operand (128 x K, the gathered rows of c) is written to
+//     shared memory, one thread issues the 3 x K/8 tcgen05.mma into the group's
+//     TMEM accumulator and commits them to the group's mbarrier; after the wait the
+//     group's warps copy the accumulator (tcgen05.ld) over its A operand (columns
+//     XOR-swizzled by row so that the stores do not collide in one bank), and each
+//     beta string scatters through its own list into the shared sigma row (shared
+//     atomics);
 //   * the row is written to sigma (float64) once per Ia.
 // Operands use the K-major no-swizzle layout: 8-row x 16-byte core matrices,
 // adjacent in K at LBO = 128 bytes, adjacent in M/N at SBO = 32 K bytes.
@@ -34,11 +42,13 @@
 
 namespace mbe {
 
-constexpr int TC_THREADS = 256;
-constexpr int TC_M = 128;          // beta strings per tile (MMA M, TMEM lanes)
-constexpr int TC_TMEM_COLS = 256;  // accumulator columns allocated (>= N, power of two)
+constexpr int TC_THREADS = 512;
+constexpr int TC_WARPS = TC_THREADS / 32;
+constexpr int TC_M = 128;           // beta strings per tile (MMA M, TMEM lanes)
+constexpr int TC_GROUP_COLS = 256;  // accumulator columns per group (>= N)
 constexpr long long TC_SPIN = 1LL << 26;  // bounded mbarrier polls
-constexpr int TC_MAXQ = 16;  // x-quads gathered per thread: K up to 4 * 2 * TC_MAXQ = 128 list entries
+constexpr int TC_MAXK = 128;        // list entries (K) the kernel accepts
+constexpr int TC_CHUNK_Q = 8;       // x-quads a thread gathers before its stores
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -100,19 +110,29 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
     return false;
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+// One 16-column TMEM load of this warp's 32 lanes, then the wait.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Named barrier of one group (ids 1.. ; id 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int g, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;\n" ::"r"(1 + g), "r"(nthreads) : "memory");
 }
 
 struct TcArgs {
-    int P, Ns, R, Np, Kp;
+    int P, Ns, R, Np, Kp, G;
     const int32_t *tab;  // [Ns][R] replacement lists
     const float *V32;    // [P][P]
     const float *c;      // [Ns][Ns] float32 coefficients
@@ -121,11 +141,14 @@ struct TcArgs {
 };
 
 struct TcSmem {
-    uint32_t off_bhi, off_blo, off_ahi, off_alo, off_T, off_row, off_jx, off_bar, off_tmem, bytes;
-    int Ts;  // row stride (floats) of the staged accumulator tile
+    uint32_t off_bhi, off_blo, off_a[2], off_T[2], off_row, off_jx, off_bar, off_tmem, off_flag, bytes;
+    int Ts;    // row stride (floats) of the staged accumulator tile
+    int swz;   // 15: columns XOR-swizzled by (row & 15) (even stride); 0: none (odd stride)
 };
 
-__host__ __device__ inline TcSmem tc_smem(int Np, int Kp, int Ns, int R)
+// G groups: B (hi, lo) shared; per group an A operand (hi, lo), over which the
+// accumulator tile [TC_M][Ts] is staged when it fits there.
+__host__ __device__ inline TcSmem tc_smem(int Np, int Kp, int Ns, int R, int G)
 {
     TcSmem S;
     uint32_t o = 0;
@@ -137,16 +160,23 @@ __host__ __device__ inline TcSmem tc_smem(int Np, int Kp, int Ns, int R)
     };
     S.off_bhi = take((uint32_t)Np * Kp * 4, 1024);
     S.off_blo = take((uint32_t)Np * Kp * 4, 1024);
-    S.off_ahi = take((uint32_t)TC_M * Kp * 4, 1024);
-    S.off_alo = take((uint32_t)TC_M * Kp * 4, 1024);
-    // the accumulator tile [TC_M][Ts] lies over the A operand (2 x TC_M x Kp floats)
-    // when it fits there; the odd stride Np + 1 avoids shared-memory bank conflicts
-    S.Ts = (Np + 1 <= 2 * Kp || Np > 2 * Kp) ? Np + 1 : Np;
-    S.off_T = (S.Ts <= 2 * Kp) ? S.off_ahi : take((uint32_t)TC_M * S.Ts * 4, 16);
+    // an odd stride Np + 1 spreads a warp's column stores over the banks; where only
+    // Np fits over A, the XOR swizzle of the column (within its 16-column block,
+    // Np being a multiple of 16) does it instead
+    const bool over_a = Np <= 2 * Kp;
+    S.Ts = (Np + 1 <= 2 * Kp || !over_a) ? Np + 1 : Np;
+    S.swz = (S.Ts & 1) ? 0 : 15;
+    for (int g = 0; g < 2; ++g) {
+        S.off_a[g] = S.off_T[g] = 0;
+        if (g >= G) continue;
+        S.off_a[g] = take((uint32_t)2 * TC_M * Kp * 4, 1024);
+        S.off_T[g] = over_a ? S.off_a[g] : take((uint32_t)TC_M * S.Ts * 4, 16);
+    }
     S.off_row = take((uint32_t)Ns * 4, 16);
     S.off_jx = take((uint32_t)R * 4, 16);
-    S.off_bar = take(8, 8);
+    S.off_bar = take(16, 8);
     S.off_tmem = take(4, 4);
+    S.off_flag = take(4 * 4, 4);
     S.bytes = (o + 127) / 128 * 128;
     return S;
 }
@@ -154,42 +184,53 @@ __host__ __device__ inline TcSmem tc_smem(int Np, int Kp, int Ns, int R)
 __global__ void __launch_bounds__(TC_THREADS, 1) k_large_ab_tc(TcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const TcSmem S = tc_smem(a.Np, a.Kp, a.Ns, a.R);
+    const int G = a.G;
+    const TcSmem S = tc_smem(a.Np, a.Kp, a.Ns, a.R, G);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int P = a.P, Ns = a.Ns, R = a.R, Np = a.Np, Kp = a.Kp;
+    const int W = TC_WARPS / G;                 // warps per group
+    const int g = warp / W, wg = warp - g * W;  // group, warp within the group
+    const int gthreads = 32 * W, tig = tid - g * gthreads;
+    const int TPR = W / 4;                      // threads per beta string of a tile
     unsigned char *bhi = smem + S.off_bhi, *blo = smem + S.off_blo;
-    unsigned char *ahi = smem + S.off_ahi, *alo = smem + S.off_alo;
+    unsigned char *ahi = smem + S.off_a[g], *alo = ahi + (size_t)TC_M * Kp * 4;
+    float *T = (float *)(smem + S.off_T[g]);
     float *row = (float *)(smem + S.off_row);
     int *jx = (int *)(smem + S.off_jx);
-    const uint32_t bar = smem_u32(smem + S.off_bar);
+    const uint32_t bar = smem_u32(smem + S.off_bar) + 8u * (uint32_t)g;
     uint32_t *tslot = (uint32_t *)(smem + S.off_tmem);
-    __shared__ int s_ok;
+    int *flag = (int *)(smem + S.off_flag);  // [0]: a wait ran out; [1 + g]: group g's last wait succeeded
+    const uint32_t ncols = (uint32_t)(TC_GROUP_COLS * G);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
-                     "r"(TC_TMEM_COLS));
+                     "r"(ncols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar));
+        for (int i = 0; i < G; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(smem + S.off_bar) + 8u * i));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        flag[0] = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const uint32_t tmem = *tslot;
+    const uint32_t tmem = *tslot + (uint32_t)(g * TC_GROUP_COLS);
     const uint32_t idesc = tf32_idesc(TC_M, Np);
     const uint32_t lbo = 128, sbo = 32u * (uint32_t)Kp;
+    const int ntiles = (Ns + TC_M - 1) / TC_M, nq = Kp / 4;
     uint32_t phase = 0;
-    bool ok = true;
 
-    for (int Ia = blockIdx.x; Ia < Ns && ok; Ia += gridDim.x) {
+    for (int Ia = blockIdx.x; Ia < Ns; Ia += gridDim.x) {
         const int32_t *ta = a.tab + (size_t)Ia * R;
         for (int x = tid; x < R; x += TC_THREADS) jx[x] = entry_J(ta[x]);
         for (int i = tid; i < Ns; i += TC_THREADS) row[i] = 0.f;
-        // B operand: B[p][x] = s_x V[p_x][p] (zero beyond P and R), hi and lo
-        for (int i = tid; i < Np * (Kp / 4); i += TC_THREADS) {
-            const int p = i / (Kp / 4), x0 = (i - p * (Kp / 4)) * 4;
+        // B operand: B[p][x] = s_x V[p_x][p] (zero beyond P and R), hi and lo;
+        // consecutive threads take consecutive pairs p (coalesced V loads, and
+        // float4 stores that fill whole 128-byte rows of banks)
+        for (int i = tid; i < Np * nq; i += TC_THREADS) {
+            const int x0 = (i / Np) * 4, p = i - (i / Np) * Np;
             float4 h, l;
             float *hv = &h.x, *lv = &l.x;
 #pragma unroll
@@ -207,39 +248,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_large_ab_tc(TcArgs a)
             *(float4 *)(blo + kmajor_off(p, x0, Kp)) = l;
         }
         __syncthreads();
-        for (int Jb0 = 0; Jb0 < Ns; Jb0 += TC_M) {
-            // A operand: A[jb][x] = c[J_x][Jb0 + jb] (zero beyond Ns and R), hi and lo.
-            // Thread (jb, q) gathers the quads x = 4q, 4(q + 2), ...: every load of
-            // the tile is issued before the first shared-memory store.
-            {
-                const int jb = tid & (TC_M - 1), q0 = tid >> 7, Jb = Jb0 + jb;
-                float g[TC_MAXQ][4];
+        for (int tile = g; tile < ntiles; tile += G) {
+            const int Jb0 = tile * TC_M;
+            const int jb = tig & (TC_M - 1), q0 = tig >> 7, Jb = Jb0 + jb;
+            // A operand: A[jb][x] = c[J_x][Jb0 + jb] (zero beyond Ns and R), hi and lo;
+            // a thread issues the loads of TC_CHUNK_Q quads before their stores
+            for (int qb = q0; qb < nq; qb += TC_CHUNK_Q * TPR) {
+                float v[TC_CHUNK_Q][4];
 #pragma unroll
-                for (int i = 0; i < TC_MAXQ; ++i) {
-                    const int x0 = 4 * (q0 + 2 * i);
+                for (int i = 0; i < TC_CHUNK_Q; ++i) {
+                    const int q = qb + i * TPR;
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const int x = x0 + j;
-                        g[i][j] = (x0 < Kp && Jb < Ns && x < R) ? __ldg(a.c + (size_t)jx[x] * Ns + Jb) : 0.f;
+                        const int x = 4 * q + j;
+                        v[i][j] = (q < nq && Jb < Ns && x < R) ? __ldg(a.c + (size_t)jx[x] * Ns + Jb) : 0.f;
                     }
                 }
 #pragma unroll
-                for (int i = 0; i < TC_MAXQ; ++i) {
-                    const int x0 = 4 * (q0 + 2 * i);
-                    if (x0 < Kp) {
+                for (int i = 0; i < TC_CHUNK_Q; ++i) {
+                    const int q = qb + i * TPR;
+                    if (q < nq) {
                         float4 h, l;
-                        split_tf32(g[i][0], h.x, l.x);
-                        split_tf32(g[i][1], h.y, l.y);
-                        split_tf32(g[i][2], h.z, l.z);
-                        split_tf32(g[i][3], h.w, l.w);
-                        *(float4 *)(ahi + kmajor_off(jb, x0, Kp)) = h;
-                        *(float4 *)(alo + kmajor_off(jb, x0, Kp)) = l;
+                        split_tf32(v[i][0], h.x, l.x);
+                        split_tf32(v[i][1], h.y, l.y);
+                        split_tf32(v[i][2], h.z, l.z);
+                        split_tf32(v[i][3], h.w, l.w);
+                        *(float4 *)(ahi + kmajor_off(jb, 4 * q, Kp)) = h;
+                        *(float4 *)(alo + kmajor_off(jb, 4 * q, Kp)) = l;
                     }
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
+            group_sync(g, gthreads);
+            if (tig == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t ah = smem_u32(ahi), al = smem_u32(alo), bh = smem_u32(bhi), bl = smem_u32(blo);
                 for (int s = 0; s < Kp / 8; ++s) {
@@ -251,65 +292,71 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_large_ab_tc(TcArgs a)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                                  bar)
                              : "memory");
-                // one thread waits (bounded) and hands the outcome to the block
-                s_ok = mbar_wait(bar, phase) ? 1 : 0;
-                if (!s_ok) atomicExch(a.err, 1);
+                // one thread waits (bounded) and hands the outcome to its group; after a
+                // wait that ran out it waits once more (bounded) for the MMAs in flight
+                // before the kernel goes on to free the accumulator
+                bool ok = mbar_wait(bar, phase);
+                if (!ok) {
+                    atomicExch(a.err, 1);
+                    atomicExch(&flag[0], 1);
+                    mbar_wait(bar, phase);
+                }
+                flag[1 + g] = ok ? 1 : 0;
+                phase ^= 1u;
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             }
-            __syncthreads();
-            if (!s_ok) {
-                ok = false;
-                break;
-            }
-            phase ^= 1u;
+            group_sync(g, gthreads);
+            if (!flag[1 + g]) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            // epilogue 1: the accumulator tile T[jb][p] to shared memory, over the A
-            // operand (free once the MMAs completed); warp w reads TMEM lanes
-            // 32 (w % 4) .. + 31, half (w / 4) of the columns
-            float *T = (float *)(smem + S.off_T);  // [TC_M][S.Ts]
+            // epilogue 1: the accumulator tile to T[jb][col ^ swz(jb)] over the A
+            // operand (free once the MMAs completed); warp wg reads TMEM lanes
+            // 32 (warp % 4) .. + 31 (the lanes its position in the warpgroup may
+            // access), the columns split between the W / 4 warps that share them
             {
-                const int jb = (warp & 3) * 32 + lane;
-                const int half = Np / 16;  // column chunks of 8 in the first half
-                const int c0 = (warp >> 2) ? half : 0, c1 = (warp >> 2) ? Np / 8 : half;
+                const int jr = (warp & 3) * 32 + lane;
+                const int sw = S.swz ? (jr & S.swz) : 0;
+                const int nch = Np / 16, part = wg >> 2;
+                const int c0 = part * nch / TPR, c1 = (part + 1) * nch / TPR;
                 const uint32_t tbase = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+                float *Tr = T + jr * S.Ts;
                 for (int ch = c0; ch < c1; ++ch) {
-                    float v[8];
-                    tmem_ld8(tbase + (uint32_t)(ch * 8), v);
+                    float v[16];
+                    tmem_ld16(tbase + (uint32_t)(ch * 16), v);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) T[jb * S.Ts + ch * 8 + i] = v[i];
+                    for (int i = 0; i < 16; ++i) Tr[ch * 16 + (i ^ sw)] = v[i];
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-            __syncthreads();
-            // epilogue 2: each beta string Jb of the tile walks its own list, E_pq|Jb> =
-            // s|K>: sigma[Ia][K] += s T[Jb][pair(p,q)] (shared atomics); two threads per
-            // string split the list
-            {
-                const int jb = tid & (TC_M - 1), part = tid >> 7, Jb = Jb0 + jb;
-                if (Jb < Ns) {
-                    const int32_t *tb = a.tab + (size_t)Jb * R;
-                    const float *Trow = T + jb * S.Ts;
-                    for (int y = part; y < R; y += 2) {
-                        const int e = __ldg(tb + y);
-                        const float v = Trow[entry_pair(e)];
-                        atomicAdd(&row[entry_J(e)], entry_neg(e) ? -v : v);
-                    }
+            group_sync(g, gthreads);
+            // epilogue 2: each beta string Jb of the tile walks its own list, E_p|Jb> =
+            // s|K>: sigma[Ia][K] += s T[Jb][p] (shared atomics); TPR threads per string
+            if (Jb < Ns) {
+                const int32_t *tb = a.tab + (size_t)Jb * R;
+                const float *Trow = T + jb * S.Ts;
+                const int sw = S.swz ? (jb & S.swz) : 0;
+                for (int y = q0; y < R; y += TPR) {
+                    const int e = __ldg(tb + y);
+                    const float v = Trow[entry_pair(e) ^ sw];
+                    atomicAdd(&row[entry_J(e)], entry_neg(e) ? -v : v);
                 }
             }
-            __syncthreads();
+            group_sync(g, gthreads);
         }
         __syncthreads();
-        if (ok)
+        const bool failed = flag[0] != 0;
+        if (!failed)
             for (int K = tid; K < Ns; K += TC_THREADS) a.sigma[(size_t)Ia * Ns + K] = (double)row[K];
         __syncthreads();
+        if (failed) break;
     }
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(*tslot), "r"(ncols));
 }
 
 }  // namespace mbe
 
-// Host side: shape checks, shared-memory size and the launch (one CTA per SM).
+// Host side: shape checks, the group count, shared-memory size and the launch
+// (one CTA per SM).
 int mbe::large_ab_tc(cudaStream_t st, int sm_count, size_t smem_optin, int P, int Ns, int R, const int32_t *tab,
                      const float *V32, const float *c, double *sigma, int *err)
 {
@@ -324,11 +371,15 @@ int mbe::large_ab_tc(cudaStream_t st, int sm_count, size_t smem_optin, int P, in
     a.c = c;
     a.sigma = sigma;
     a.err = err;
-    // the gather holds up to 8 TC_MAXQ list entries per thread
-    MBE_CHECK(a.Np >= 16 && a.Np <= TC_TMEM_COLS && a.Kp >= 8 && a.Kp <= 8 * TC_MAXQ, MBE_EUNSUPPORTED,
-              "large CASCI: tensor-core sigma needs at most %d pairs and %d list entries (got %d, %d)", TC_TMEM_COLS,
-              8 * TC_MAXQ, P, R);
-    const TcSmem S = tc_smem(a.Np, a.Kp, Ns, R);
+    MBE_CHECK(a.Np >= 16 && a.Np <= TC_GROUP_COLS && a.Kp >= 8 && a.Kp <= TC_MAXK, MBE_EUNSUPPORTED,
+              "large CASCI: tensor-core sigma needs at most %d pairs and %d list entries (got %d, %d)", TC_GROUP_COLS,
+              TC_MAXK, P, R);
+    a.G = 2;
+    TcSmem S = tc_smem(a.Np, a.Kp, Ns, R, a.G);
+    if (S.bytes + 1024 > smem_optin) {
+        a.G = 1;
+        S = tc_smem(a.Np, a.Kp, Ns, R, a.G);
+    }
     MBE_CHECK(S.bytes + 1024 <= smem_optin, MBE_EUNSUPPORTED, "large CASCI: tensor-core sigma needs %u B shared memory",
               S.bytes);
     MBE_CU(cudaFuncSetAttribute(k_large_ab_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.bytes));
