@@ -80,10 +80,11 @@ def sigma_flops_per_det(n: int, k: int) -> int:
 DAVIDSON_FLOPS_PER_DET = 72  # residual, preconditioner, 2-pass orthogonalisation, 3x3 projections, update
 
 
-def solver_bucket(n: int, k: int):
-    """(solver, dpl) the library uses for a class: warp solver for <= 416 determinants."""
+def solver_bucket(n: int, k: int, warp_max_ndet: int = 416):
+    """(solver, dpl) the library uses for a class: the warp solver up to the tuned
+    determinant limit (mbe_tuning.warp_max_ndet), else the block solver."""
     N = math.comb(n, k) ** 2
-    if n <= 8 and N <= 416:
+    if n <= 8 and N <= warp_max_ndet:
         for d in (1, 2, 4, 8, 13):
             if d * 32 >= N:
                 return 0, d
@@ -403,7 +404,7 @@ def run_ours(args):
     # ---- roofline of the dominant solver kernel (per launch, CUDA events inside the library)
     occ_np = np.asarray(w.occ)
 
-    def roofline_of(recs, out, total_ms):
+    def roofline_of(recs, out, total_ms, prec):
         per_bucket = {}
         for (order, solver, dpl, ms) in recs:
             per_bucket.setdefault((order, solver, dpl), []).append(ms)
@@ -414,9 +415,10 @@ def run_ours(args):
         iters = out["iters"][i].cpu().numpy()
         kk = occ_np[tup].sum(axis=1)
         n = len(w.ref) + order
+        warp_max = ctx.get_tuning(prec, n)["warp_max_ndet"]
         f64 = f32 = 0.0
         for k in np.unique(kk):
-            if solver_bucket(n, int(k)) != (solver, dpl):
+            if solver_bucket(n, int(k), warp_max) != (solver, dpl):
                 continue
             sel = kk == k
             # a sigma product computes the Ns(Ns+1)/2 determinants with Ia <= Ib (the rest
@@ -448,8 +450,8 @@ def run_ours(args):
                 "fp64_tflops": f64 / t_s / 1e12, "fp32_tflops": f32 / t_s / 1e12,
                 "share_of_step": sum(per_bucket[key]) / total_ms}
 
-    roofline = roofline_of(recs_mix, out_mix, sum(ms_mix))
-    roofline_64 = roofline_of(recs_64, out_64, sum(ms_64))
+    roofline = roofline_of(recs_mix, out_mix, sum(ms_mix), "mixed")
+    roofline_64 = roofline_of(recs_64, out_64, sum(ms_64), "fp64")
 
     # ---- end to end through the public API with host inputs
     h1_h = torch.tensor(w.h1).pin_memory()
