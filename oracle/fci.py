@@ -243,3 +243,60 @@ def lowest_eigenvalue_even(h: np.ndarray, eri: np.ndarray, ne: int, tol: float =
     w = scipy.sparse.linalg.eigsh(Hq, k=1, which="SA", tol=tol, v0=v0, ncv=min(Hq.shape[0], 40),
                                   return_eigenvectors=False)
     return float(w[0])
+
+
+def s2_dense(n: int, na: int, nb: int) -> np.ndarray:
+    """Total spin S^2 in the (na, nb) determinant basis (index I_a * N_b + I_b).
+
+    State targeting (the paper converges its Cr2 expansion onto the 1Sigma_g+
+    ground state) needs the spin of a CASCI state; S^2 is written out here from
+    its second-quantised form, S^2 = S_- S_+ + S_z (S_z + 1), with
+    S_+ = sum_p a+_{p,alpha} a_{p,beta}, S_- = sum_p a+_{p,beta} a_{p,alpha} and
+    S_z = (na - nb) / 2.  Each creator or annihilator acts on the 2n-bit
+    determinant word (alpha spin orbitals 0..n-1, beta n..2n-1) with the sign
+    (-1)^(occupied spin orbitals below it), the convention of the Hamiltonian.
+    Dense; small spaces only."""
+    words = [int(w) for w in dets(n, na, nb)]
+    index = {w: i for i, w in enumerate(words)}
+    N = len(words)
+    S2 = np.zeros((N, N))
+
+    def hop(w: int, create: int, annihilate: int):
+        """a+_create a_annihilate |w>: (sign, word), or None when it vanishes."""
+        if not (w >> annihilate) & 1:
+            return None
+        s = bin(w & ((1 << annihilate) - 1)).count("1")
+        w1 = w & ~(1 << annihilate)
+        if (w1 >> create) & 1:
+            return None
+        s += bin(w1 & ((1 << create) - 1)).count("1")
+        return (-1.0 if s & 1 else 1.0), w1 | (1 << create)
+
+    sz = 0.5 * (na - nb)
+    for j, w in enumerate(words):
+        S2[j, j] += sz * (sz + 1.0)
+        for p in range(n):  # S_+: the beta electron of orbital p becomes alpha
+            r1 = hop(w, p, n + p)
+            if r1 is None:
+                continue
+            for q in range(n):  # S_-: the alpha electron of orbital q becomes beta
+                r2 = hop(r1[1], n + q, q)
+                if r2 is None:
+                    continue
+                S2[index[r2[1]], j] += r1[0] * r2[0]
+    return S2
+
+
+def lowest_eigenvalue_spin(h: np.ndarray, eri: np.ndarray, ne: int, spin: float = 0.0) -> float:
+    """Lowest eigenvalue of the CAS Hamiltonian (n_alpha = n_beta = ne) among the
+    states of total spin S = `spin`: H restricted to the eigenspace of S^2 with
+    eigenvalue S(S+1) (H and S^2 commute), by LAPACK.  Dense; small spaces only."""
+    import scipy.linalg
+
+    n = h.shape[0]
+    H = h_dense(h, eri, ne, ne)
+    w, U = scipy.linalg.eigh(s2_dense(n, ne, ne))
+    Q = U[:, np.abs(w - spin * (spin + 1.0)) < 1e-6]
+    if Q.shape[1] == 0:
+        raise ValueError(f"no state of spin {spin} in this space")
+    return float(scipy.linalg.eigh(Q.T @ H @ Q, eigvals_only=True, subset_by_index=[0, 0])[0])
