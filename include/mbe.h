@@ -94,13 +94,24 @@ typedef struct mbe_opts {
                              under the exchange of the alpha and beta strings (the
                              closed-shell determinant's sector; for n_alpha = n_beta
                              the states of even total spin)                         */
+    double s2_penalty;    /* state targeting by total spin (the paper converges its
+                             Cr2 expansion onto a singlet, 1Sigma_g+): mu >= 0; the
+                             solvers find the lowest eigenvalue of H + mu S^2.  A
+                             singlet's energy is unchanged (S^2 = 0) and a state of
+                             spin S is raised by mu S(S+1), so with mu above the
+                             largest singlet-high-spin gap the result is the lowest
+                             singlet energy.  0 (default): off.  casci_batch and
+                             casci_rdm_batch only; casci_solve (and the tuples that
+                             casci_batch_routed hands to it) reject mu != 0 with
+                             MBE_EUNSUPPORTED.  Costs up to k^2 extra terms per
+                             determinant in every sigma product.                   */
 } mbe_opts;
 
 #define MBE_SECTORS_BOTH 0
 #define MBE_SECTORS_EVEN 1
 
 /* Fills *opts with the defaults: FP64, tol 1e-7, tol_switch 1e-5, max_iter 2000,
-   fp64_final_iters 2, MBE_SECTORS_BOTH.  Host only, synchronous.  The residual
+   fp64_final_iters 2, MBE_SECTORS_BOTH, s2_penalty 0.  Host only, synchronous.  The residual
    tolerance 1e-7 keeps every tuple energy within ~1e-13 E_h of the exact lowest
    eigenvalue (the error is about |r|^2 / gap), which the Eq. 2 sums need: the
    Rayleigh-quotient errors of ~10^5 tuples all have the same sign. */

@@ -39,7 +39,8 @@ EXPORTS = ("mbe_default_opts", "mbe_ctx_create", "mbe_ctx_set_stream", "mbe_ctx_
 class MbeOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("tol_switch", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("fp64_final_iters", ctypes.c_int), ("sectors", ctypes.c_int)]
+                ("fp64_final_iters", ctypes.c_int), ("sectors", ctypes.c_int),
+                ("s2_penalty", ctypes.c_double)]
 
 
 class MbeTiming(ctypes.Structure):
@@ -160,6 +161,7 @@ class Opts:
     max_iter: int = 2000
     fp64_final_iters: int = 2
     even_only: bool = False  # only the even sector of the alpha-beta string exchange
+    s2_penalty: float = 0.0  # mu of H + mu S^2 (state targeting by total spin; 0: off)
 
     def to_c(self) -> MbeOpts:
         o = MbeOpts()
@@ -169,6 +171,7 @@ class Opts:
         o.max_iter = self.max_iter
         o.fp64_final_iters = self.fp64_final_iters
         o.sectors = 1 if self.even_only else 0
+        o.s2_penalty = self.s2_penalty
         return o
 
 

@@ -121,7 +121,8 @@ static int run_casci(mbe_ctx *ctx, int norb, const double *h1, const double *eri
     MBE_CHECK(o.precision == MBE_PREC_FP64 || o.precision == MBE_PREC_MIXED, MBE_EINVAL,
               "casci_batch: unknown precision %d", o.precision);
     MBE_CHECK(o.tol > 0 && o.tol_switch > 0 && o.max_iter >= 1 && o.fp64_final_iters >= 0 &&
-                  (o.sectors == MBE_SECTORS_BOTH || o.sectors == MBE_SECTORS_EVEN), MBE_EINVAL,
+                  (o.sectors == MBE_SECTORS_BOTH || o.sectors == MBE_SECTORS_EVEN) &&
+                  o.s2_penalty >= 0.0 && o.s2_penalty < 1e6, MBE_EINVAL,
               "casci_batch: bad options");
     if (n_tuples == 0) return MBE_OK;
     MBE_CHECK(rdm || (eps_out != nullptr && status_out != nullptr), MBE_EINVAL, "casci_batch: NULL output");
@@ -153,6 +154,7 @@ static int run_casci(mbe_ctx *ctx, int norb, const double *h1, const double *eri
     a.max_iter = o.max_iter;
     a.min_fp64 = o.fp64_final_iters;
     a.even_only = o.sectors == MBE_SECTORS_EVEN ? 1 : 0;
+    a.s2mu = o.s2_penalty;
     const mbe_tuning tu = ctx->tune[o.precision == MBE_PREC_MIXED ? 1 : 0][n];
     a.warps = tu.warp_warps;
     a.block_basis = tu.block_basis;

@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
         pb.diag = (double *)(slot + L.off_diag);
         pb.c = nullptr;
         const bool mixed = a.precision == MBE_PREC_MIXED;
+        pb.s2mu = a.s2mu;
         setup_problem<BlockGroup>(a, pb, mixed);
         uint32_t mphi = 0;
         for (int i = 0; i < n; ++i)

@@ -68,6 +68,7 @@ struct BatchArgs {
     double tol, tol_switch;
     int max_iter, min_fp64;
     int even_only;  // solve the even spin-flip sector only
+    double s2mu;    // S^2 penalty: the solvers work on H + s2mu S^2 (0: off)
     double *eps;
     int32_t *status;
     int32_t *iters;
@@ -148,6 +149,7 @@ struct Problem {
     void *c;              // [N] vector sigma reads (T)
     void *sbuf;           // [N] sigma output staging (warp solver)
     int sector;           // spin-flip sector of the solver's vectors (+1 or -1)
+    double s2mu = 0.0;    // S^2 penalty (state targeting): sigma of H + s2mu S^2
 };
 
 // Symmetric counterpart of determinant d = Ia * Ns + Ib under the exchange of the
@@ -276,6 +278,8 @@ __device__ void setup_problem(const BatchArgs &a, Problem &pb, bool want32)
                 v += pb.V64[pair_index(p, p) * P + pair_index(q, q)];
             }
         }
+        // S^2 penalty: mu times the number of alpha-only orbitals
+        v += pb.s2mu * __popc(pb.str[ia] & ~pb.str[ib]);
         pb.diag[d] = v;
     }
     G::sync();
@@ -291,6 +295,59 @@ __device__ inline float flip_if(float v, int neg) { return __int_as_float(__floa
 
 // a5: one element of sigma = H c, accumulated in T; the vector c may be stored
 // in a narrower type TV (the float64 sigma of a float32 anchor vector).
+// (S^2 c)[Ia][Ib] for n_alpha = n_beta = k.  With S^2 = S_- S_+ (S_z = 0) and the
+// alpha and beta operators ordered apart, S^2 = k - sum_pq E^a_pq E^b_qp: the
+// number of alpha-only orbitals times c[Ia][Ib], minus for every alpha-only p
+// and beta-only q the spin exchange c[Ia - p + q][Ib - q + p], signed by the two
+// single replacements.  Those are read from the strings' replacement lists: the
+// entry that empties occupied orbital o and fills u sits at (number of occupied
+// orbitals below o) * (n - k + 1) + (number of empty orbitals below u) + (o < u).
+template <typename T, typename TV>
+__device__ inline T s2_elem(const Problem &pb, const TV *__restrict__ c, int ia, int ib)
+{
+    const uint32_t sa = pb.str[ia], sb = pb.str[ib];
+    const uint32_t ao = sa & ~sb, bo = sb & ~sa;
+    const int Ns = pb.Ns, w = pb.n - pb.k + 1;
+    const uint32_t full = (1u << pb.n) - 1u;
+    const int32_t *ta = pb.tab + ia * pb.RS, *tb = pb.tab + ib * pb.RS;
+    T acc = (T)__popc(ao) * (T)c[ia * Ns + ib];
+    for (uint32_t pm = ao; pm; pm &= pm - 1u) {
+        const int p = __ffs((int)pm) - 1;
+        const uint32_t below_p = (1u << p) - 1u;
+        const int xa = __popc(sa & below_p) * w, yb = __popc(~sb & full & below_p);
+        for (uint32_t qm = bo; qm; qm &= qm - 1u) {
+            const int q = __ffs((int)qm) - 1;
+            const uint32_t below_q = (1u << q) - 1u;
+            const int32_t ea = ta[xa + __popc(~sa & full & below_q) + (p < q ? 1 : 0)];
+            const int32_t eb = tb[__popc(sb & below_q) * w + yb + (q < p ? 1 : 0)];
+            acc -= flip_if((T)c[entry_J(ea) * Ns + entry_J(eb)], entry_neg(ea) ^ entry_neg(eb));
+        }
+    }
+    return acc;
+}
+
+// Adds mu (S^2 c) to a sigma over the half space (the elements with Ia <= Ib,
+// mirrored like the sigma itself).  A separate pass, taken only with the penalty
+// on, keeps the sigma's inner loop free of it; each thread revisits the elements
+// it computed in the sigma pass, so no synchronisation is needed in between.
+template <typename T, typename TV>
+__device__ inline void add_s2_half(const Problem &pb, const TV *__restrict__ c, T *sbuf, int first, int stride)
+{
+    const int Ns = pb.Ns, nh = Ns * (Ns + 1) / 2;
+    int ia = 0, ib = 0;
+    tri_advance(ia, ib, first, Ns);
+#pragma unroll 1
+    for (int h = first; h < nh; h += stride) {
+        if (!(pb.sector < 0 && ia == ib)) {
+            const int d = ia * Ns + ib, pd = ib * Ns + ia;
+            const T v = (T)pb.s2mu * s2_elem<T, TV>(pb, c, ia, ib);
+            sbuf[d] += v;
+            if (pd != d) sbuf[pd] += pb.sector > 0 ? v : -v;
+        }
+        tri_advance(ia, ib, stride, Ns);
+    }
+}
+
 template <typename T, typename TV = T>
 __device__ inline T sigma_elem(const Problem &pb, const T *__restrict__ V, const T *__restrict__ Hs,
                                const TV *__restrict__ c, int d)
@@ -602,6 +659,7 @@ __device__ inline void sigma_warp(const Problem &pb, const T *V, const T *Hs, co
         if (pd != d) sbuf[pd] = pb.sector > 0 ? v : -v;
         tri_advance(ia, ib, 32, Ns);
     }
+    if (pb.s2mu != 0.0) add_s2_half<T, TV>(pb, c, sbuf, lane, 32);
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < DPL; ++j) {
@@ -1044,6 +1102,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
         pb.sbuf = (void *)(ws + L.off_s);
         __syncwarp();
         const bool mixed = a.precision == MBE_PREC_MIXED;
+        pb.s2mu = a.s2mu;
         setup_problem<WarpGroup>(a, pb, mixed);
         // Phi_A: the in-space occupied orbitals
         uint32_t mphi = 0;
@@ -1259,6 +1318,7 @@ __device__ inline void sigma_warp_anchor(const Problem &pb, const double *Vp, co
         if (pd != d) sbuf[pd] = pb.sector > 0 ? v : -v;
         tri_advance(ia, ib, 32, Ns);
     }
+    if (pb.s2mu != 0.0) add_s2_half<double, double>(pb, c, sbuf, lane, 32);
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < DPL; ++j) {
@@ -1391,6 +1451,7 @@ static __device__ void setup_mix(const BatchArgs &a, Problem &pb, char *ws, cons
                 v += Vp[tri_index(pair_index(p, p), pair_index(q, q))];
             }
         }
+        v += pb.s2mu * __popc(pb.str[ia] & ~pb.str[ib]);
         diag64[d] = v;
         d32[d] = (float)v;
     }
@@ -1456,6 +1517,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 3)
         pb.c = (void *)(ws + L.off_c);
         pb.sbuf = (void *)(ws + L.off_s);
         __syncwarp();
+        pb.s2mu = a.s2mu;
         setup_mix(a, pb, ws, L, Vp, Hsp, diag64);
         uint32_t mphi = 0;
         for (int i = 0; i < n; ++i)
@@ -1865,6 +1927,7 @@ __device__ inline void sigma_block(const Problem &pb, const T *Vi, const T *Hs, 
         if (pd != d) dst[pd] = pb.sector > 0 ? v : -v;
         tri_advance(ia, ib, blockDim.x, Ns);
     }
+    if (pb.s2mu != 0.0) add_s2_half<T, T>(pb, src, dst, threadIdx.x, blockDim.x);
     __syncthreads();
 }
 

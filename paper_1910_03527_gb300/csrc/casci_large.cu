@@ -1021,6 +1021,7 @@ extern "C" int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const doubl
     MBE_CHECK(o.tol > 0 && o.tol_switch > 0 && o.max_iter >= 1 && o.fp64_final_iters >= 0 &&
                   (o.sectors == MBE_SECTORS_BOTH || o.sectors == MBE_SECTORS_EVEN), MBE_EINVAL,
               "casci_solve: bad options");
+    MBE_CHECK(o.s2_penalty == 0.0, MBE_EUNSUPPORTED, "casci_solve: the S^2 penalty is not supported for one large CAS");
     MBE_CU(cudaSetDevice(ctx->device));
     std::vector<uint8_t> occ_h(norb);
     MBE_CU(cudaMemcpyAsync(occ_h.data(), occ, norb, cudaMemcpyDeviceToHost, ctx->stream));

@@ -131,6 +131,7 @@ void mbe_default_opts(mbe_opts *o)
     o->max_iter = 2000;
     o->fp64_final_iters = 2;
     o->sectors = MBE_SECTORS_BOTH;
+    o->s2_penalty = 0.0;
 }
 
 const char *mbe_last_error(void) { return g_err; }
