@@ -327,11 +327,12 @@ __device__ inline T s2_elem(const Problem &pb, const TV *__restrict__ c, int ia,
 }
 
 // Adds mu (S^2 c) to a sigma over the half space (the elements with Ia <= Ib,
-// mirrored like the sigma itself).  A separate pass, taken only with the penalty
-// on, keeps the sigma's inner loop free of it; each thread revisits the elements
-// it computed in the sigma pass, so no synchronisation is needed in between.
+// mirrored like the sigma itself).  A separate pass, out of line and taken only
+// with the penalty on, keeps the sigma's inner loop and its register allocation
+// as they are without it; each thread revisits the elements it computed in the
+// sigma pass, so no synchronisation is needed in between.
 template <typename T, typename TV>
-__device__ inline void add_s2_half(const Problem &pb, const TV *__restrict__ c, T *sbuf, int first, int stride)
+__device__ __noinline__ void add_s2_half(const Problem &pb, const TV *__restrict__ c, T *sbuf, int first, int stride)
 {
     const int Ns = pb.Ns, nh = Ns * (Ns + 1) / 2;
     int ia = 0, ib = 0;
@@ -1459,7 +1460,9 @@ static __device__ void setup_mix(const BatchArgs &a, Problem &pb, char *ws, cons
 }
 
 template <int DPL>
-__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 3)
+// Up to 8 determinants per lane the kernel fits in 128 registers, so four 4-warp
+// blocks share an SM (their shared memory allows it); at 13, three.
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, DPL <= 8 ? 4 : 3)
     k_casci_warp_mixed(BatchArgs a, int bucket, MixLayout L)
 {
     extern __shared__ __align__(16) char smem[];
