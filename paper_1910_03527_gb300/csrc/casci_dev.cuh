@@ -1459,9 +1459,10 @@ static __device__ void setup_mix(const BatchArgs &a, Problem &pb, char *ws, cons
     __syncwarp();
 }
 
-template <int DPL>
 // Up to 8 determinants per lane the kernel fits in 128 registers, so four 4-warp
-// blocks share an SM (their shared memory allows it); at 13, three.
+// blocks share an SM (their shared memory allows it); at 13, three: 128
+// registers there spill, and four blocks ran 19% slower.
+template <int DPL>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, DPL <= 8 ? 4 : 3)
     k_casci_warp_mixed(BatchArgs a, int bucket, MixLayout L)
 {
