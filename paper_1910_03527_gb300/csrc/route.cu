@@ -26,13 +26,18 @@ __global__ void k_route_scatter(int64_t n, const int64_t *rows, const double *ep
     if (iters_out) iters_out[r] = iters[i];
 }
 
-// One tuple's result: eps = (lambda - <Phi_A|H_A|Phi_A>) - E_ref,corr.
-__global__ void k_route_put(double *eps_out, int32_t *status_out, int32_t *iters_out, int64_t row, double eps_a,
-                            double e_ref_corr, int32_t status, int32_t iters)
+// The one-determinant and malformed tuples of a call, in one launch: an active
+// space whose only determinant is Phi_A has lambda = <Phi_A|H_A|Phi_A>, so
+// eps = -E_ref,corr; a malformed tuple gets NaN and MBE_STATUS_BADINPUT.
+__global__ void k_route_direct(int64_t n, const int64_t *rows, const int32_t *status, double e_ref_corr,
+                               double *eps_out, int32_t *status_out, int32_t *iters_out)
 {
-    eps_out[row] = status == MBE_STATUS_BADINPUT ? (double)NAN : eps_a - e_ref_corr;
-    status_out[row] = status;
-    if (iters_out) iters_out[row] = iters;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t r = rows[i];
+    eps_out[r] = status[i] == MBE_STATUS_BADINPUT ? (double)NAN : -e_ref_corr;
+    status_out[r] = status[i];
+    if (iters_out) iters_out[r] = 0;
 }
 
 // Stream-ordered device buffers released when the call returns, on every path.
@@ -148,29 +153,62 @@ extern "C" int casci_batch_routed(mbe_ctx *ctx, int norb, const double *h1, cons
             ctx->launches += 1;
         }
     }
-    for (int64_t t : rows_d) {
-        // A malformed tuple, or an active space whose only determinant is Phi_A
-        // (lambda = <Phi_A|H_A|Phi_A>, so eps = -E_ref,corr).
-        const int32_t *tp = tup_h.data() + (size_t)t * order;
-        bool ok = true;
-        for (int i = 0; i < order; ++i)
-            ok = ok && tp[i] >= 0 && tp[i] < norb && !in_ref[tp[i]] && (i == 0 || tp[i] > tp[i - 1]);
-        k_route_put<<<1, 1, 0, ctx->stream>>>(eps_out, status_out, iters_out, t, 0.0, e_ref_corr,
-                                              ok ? MBE_STATUS_OK : MBE_STATUS_BADINPUT, 0);
+    if (!rows_d.empty()) {
+        const int64_t nd = (int64_t)rows_d.size();
+        std::vector<int32_t> st_d(nd);
+        for (int64_t i = 0; i < nd; ++i) {
+            const int32_t *tp = tup_h.data() + (size_t)rows_d[i] * order;
+            bool ok = true;
+            for (int j = 0; j < order; ++j)
+                ok = ok && tp[j] >= 0 && tp[j] < norb && !in_ref[tp[j]] && (j == 0 || tp[j] > tp[j - 1]);
+            st_d[i] = ok ? MBE_STATUS_OK : MBE_STATUS_BADINPUT;
+        }
+        void *d_rows = nullptr, *d_st = nullptr;
+        MBE_CU(buf.get((size_t)nd * sizeof(int64_t), &d_rows));
+        MBE_CU(buf.get((size_t)nd * sizeof(int32_t), &d_st));
+        MBE_CU(cudaMemcpyAsync(d_rows, rows_d.data(), (size_t)nd * sizeof(int64_t), cudaMemcpyHostToDevice,
+                               ctx->stream));
+        MBE_CU(cudaMemcpyAsync(d_st, st_d.data(), (size_t)nd * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               ctx->stream));
+        k_route_direct<<<(unsigned)((nd + 255) / 256), 256, 0, ctx->stream>>>(
+            nd, (const int64_t *)d_rows, (const int32_t *)d_st, e_ref_corr, eps_out, status_out, iters_out);
         MBE_CU(cudaGetLastError());
         ctx->launches += 1;
     }
-    std::vector<int32_t> A(n_cas);
-    for (int64_t t : rows_l) {
-        const int32_t *tp = tup_h.data() + (size_t)t * order;
-        std::merge(ref_orbs, ref_orbs + n_ref, tp, tp + order, A.begin());
-        double result[3] = {0.0, 0.0, 0.0};
-        int32_t info[3] = {0, 0, 0};
-        int rc = casci_solve(ctx, norb, h1, eri, occ, n_cas, A.data(), opts, result, info, nullptr);
-        if (rc) return rc;
-        const int32_t iters = (std::min(info[1], 65535) << 16) | std::min(info[2], 65535);
-        k_route_put<<<1, 1, 0, ctx->stream>>>(eps_out, status_out, iters_out, t, result[1], e_ref_corr, info[0],
-                                              iters);
+    if (!rows_l.empty()) {
+        // one whole-GPU solve per tuple (casci_solve is synchronous); the results
+        // are scattered to their rows in one launch at the end
+        const int64_t nl = (int64_t)rows_l.size();
+        std::vector<double> eps_l(nl);
+        std::vector<int32_t> st_l(nl), it_l(nl);
+        std::vector<int32_t> A(n_cas);
+        for (int64_t i = 0; i < nl; ++i) {
+            const int32_t *tp = tup_h.data() + (size_t)rows_l[i] * order;
+            std::merge(ref_orbs, ref_orbs + n_ref, tp, tp + order, A.begin());
+            double result[3] = {0.0, 0.0, 0.0};
+            int32_t info[3] = {0, 0, 0};
+            int rc = casci_solve(ctx, norb, h1, eri, occ, n_cas, A.data(), opts, result, info, nullptr);
+            if (rc) return rc;
+            eps_l[i] = result[1] - e_ref_corr;
+            st_l[i] = info[0];
+            it_l[i] = (std::min(info[1], 65535) << 16) | std::min(info[2], 65535);
+        }
+        void *d_rows = nullptr, *d_eps = nullptr, *d_st = nullptr, *d_it = nullptr;
+        MBE_CU(buf.get((size_t)nl * sizeof(int64_t), &d_rows));
+        MBE_CU(buf.get((size_t)nl * sizeof(double), &d_eps));
+        MBE_CU(buf.get((size_t)nl * sizeof(int32_t), &d_st));
+        MBE_CU(buf.get((size_t)nl * sizeof(int32_t), &d_it));
+        MBE_CU(cudaMemcpyAsync(d_rows, rows_l.data(), (size_t)nl * sizeof(int64_t), cudaMemcpyHostToDevice,
+                               ctx->stream));
+        MBE_CU(cudaMemcpyAsync(d_eps, eps_l.data(), (size_t)nl * sizeof(double), cudaMemcpyHostToDevice,
+                               ctx->stream));
+        MBE_CU(cudaMemcpyAsync(d_st, st_l.data(), (size_t)nl * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               ctx->stream));
+        MBE_CU(cudaMemcpyAsync(d_it, it_l.data(), (size_t)nl * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               ctx->stream));
+        k_route_scatter<<<(unsigned)((nl + 255) / 256), 256, 0, ctx->stream>>>(
+            nl, (const int64_t *)d_rows, (const double *)d_eps, (const int32_t *)d_st, (const int32_t *)d_it,
+            eps_out, status_out, iters_out);
         MBE_CU(cudaGetLastError());
         ctx->launches += 1;
     }
