@@ -13,6 +13,11 @@
 //     V in shared memory); in float32 it is, per alpha string, a dense product of
 //     the signed V columns with the gathered rows of C followed by a scatter
 //     through the beta lists into a shared-memory sigma row;
+//   * inside the Davidson every vector lies in one spin-flip sector,
+//     c[Ia][Ib] = sgn c[Ib][Ia], and so does its sigma: the float64 opposite-spin
+//     term is computed for Ia <= Ib and mirrored, and the beta same-spin term is
+//     sgn times the transpose of the alpha one (one sparse product and a
+//     transposing add instead of two products and a transpose of c);
 //   * Davidson: the tuple solvers' algorithm (MLARGE-vector basis, thick restart
 //     on the two lowest Ritz vectors, float32 phase then float64 phase) with its
 //     vector algebra in grid-wide kernels, the projected eigenproblem in one
@@ -187,8 +192,11 @@ __global__ void k_large_diag(LargeCas L)
 //     sigma[Ia][Ib] = sum_{x in list(Ia)} s_x sum_{y in list(Ib)} s_y V[p_x][p_y] c[J_x][J_y]
 // (written, not accumulated). The beta lists are read through the transposed
 // table, so a warp's 32 consecutive Ib load 32 consecutive words.
+// sgn = +1 or -1: c lies in that spin-flip sector (c[Ia][Ib] = sgn c[Ib][Ia]), so
+// only the elements with Ia <= Ib are computed and each is mirrored, sigma[Ib][Ia]
+// = sgn sigma[Ia][Ib] (the diagonal of the odd sector vanishes); 0: every element.
 __global__ void __launch_bounds__(SIGMA_THREADS) k_large_ab64(LargeCas L, const double *__restrict__ c,
-                                                               double *__restrict__ sigma)
+                                                               double *__restrict__ sigma, int sgn)
 {
     extern __shared__ __align__(16) char smem[];
     double *Vs = (double *)smem;
@@ -197,6 +205,11 @@ __global__ void __launch_bounds__(SIGMA_THREADS) k_large_ab64(LargeCas L, const 
     __syncthreads();
     for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < L.N; d += (int64_t)gridDim.x * blockDim.x) {
         const int ia = (int)(d / Ns), ib = (int)(d - (int64_t)ia * Ns);
+        if (sgn != 0 && ia > ib) continue;
+        if (sgn < 0 && ia == ib) {
+            sigma[d] = 0.0;
+            continue;
+        }
         double acc0 = 0.0, acc1 = 0.0;
         const int32_t *ta = L.tab + (size_t)ia * R;
         const int32_t *tb = L.tabT + ib;
@@ -219,6 +232,7 @@ __global__ void __launch_bounds__(SIGMA_THREADS) k_large_ab64(LargeCas L, const 
             if (x & 1) acc1 += flip_if(s, entry_neg(ea)); else acc0 += flip_if(s, entry_neg(ea));
         }
         sigma[d] = acc0 + acc1;
+        if (sgn != 0 && ia < ib) sigma[(int64_t)ib * Ns + ia] = sgn > 0 ? acc0 + acc1 : -(acc0 + acc1);
     }
 }
 
@@ -229,7 +243,8 @@ __global__ void __launch_bounds__(SIGMA_THREADS) k_large_ab64(LargeCas L, const 
 // transposed coefficient matrix and the product is C Hs^T).
 constexpr int SS_ROWS = 32, SS_TK = 256, SS_THREADS = 256;
 
-template <typename T, bool TRANS>
+// STORE: out[I][K] = (Hs X)[I][K] instead of adding it (TRANS false only).
+template <typename T, bool TRANS, bool STORE = false>
 __global__ void __launch_bounds__(SS_THREADS) k_large_ss(LargeCas L, const T *__restrict__ X,
                                                           double *__restrict__ sigma)
 {
@@ -266,7 +281,37 @@ __global__ void __launch_bounds__(SS_THREADS) k_large_ss(LargeCas L, const T *__
             const int I = I0 + r, K = K0 + k;
             if (I < Ns && K < Ns) {
                 const size_t at = TRANS ? (size_t)K * Ns + I : (size_t)I * Ns + K;
-                sigma[at] += (double)out[r * (SS_TK + 1) + k];
+                if (STORE)
+                    sigma[at] = (double)out[r * (SS_TK + 1) + k];
+                else
+                    sigma[at] += (double)out[r * (SS_TK + 1) + k];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// sigma += A + sgn A^T for an Ns x Ns matrix A (32 x 32 tiles through shared
+// memory): the same-spin terms of a vector in the spin-flip sector sgn, whose
+// beta term is sgn times the transpose of the alpha term A = Hs C.
+__global__ void k_sym_add(const double *__restrict__ A, int Ns, int sgn, double *__restrict__ sigma)
+{
+    __shared__ double tile[32][33];
+    const int nt = (Ns + 31) / 32;
+    for (int64_t t = blockIdx.x; t < (int64_t)nt * nt; t += gridDim.x) {
+        const int bi = (int)(t / nt), bj = (int)(t - (int64_t)bi * nt);
+        // tile[x][r] = A[bj*32 + r][bi*32 + x], read row-wise (coalesced)
+        for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+            const int i = bj * 32 + r, j = bi * 32 + threadIdx.x;
+            tile[threadIdx.x][r] = (i < Ns && j < Ns) ? A[(size_t)i * Ns + j] : 0.0;
+        }
+        __syncthreads();
+        for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+            const int i = bi * 32 + r, j = bj * 32 + threadIdx.x;
+            if (i < Ns && j < Ns) {
+                const size_t at = (size_t)i * Ns + j;
+                const double at_t = tile[r][threadIdx.x];  // A[j][i]
+                sigma[at] += A[at] + (sgn > 0 ? at_t : -at_t);
             }
         }
         __syncthreads();
@@ -620,6 +665,8 @@ static int large_setup(mbe_ctx *ctx, int norb, const double *h1, const double *e
                                 (int)plan->smem_ss64));
     MBE_CU(cudaFuncSetAttribute(k_large_ss<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)plan->smem_ss64));
+    MBE_CU(cudaFuncSetAttribute(k_large_ss<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)plan->smem_ss64));
     MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_large_ss<double, false>, SS_THREADS, plan->smem_ss64));
     plan->grid_ss64 = ctx->sm_count * (b > 0 ? b : 1);
     MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_large_ss<float, false>, SS_THREADS, plan->smem_ss32));
@@ -647,13 +694,14 @@ static size_t large_bytes(int norb, int n, int k, bool dense_separate, bool fp32
 // sigma = H c: the opposite-spin term written first, then Hs C added, then C Hs^T
 // added through the transposed copy of c.
 template <typename T>
-static int large_sigma_launch(mbe_ctx *ctx, const LargePlan &pl, const T *c, double *sigma, int order_tag)
+static int large_sigma_launch(mbe_ctx *ctx, const LargePlan &pl, const T *c, double *sigma, int order_tag,
+                              int sgn = 0)
 {
     TimedLaunch tl(ctx, order_tag, 2, sizeof(T) == 8 ? 64 : 32);
     const int Ns = pl.L.Ns;
-    T *cT = (T *)pl.cT;
     if (sizeof(T) == 8) {
-        k_large_ab64<<<pl.grid_ab64, SIGMA_THREADS, pl.smem_ab64, ctx->stream>>>(pl.L, (const double *)c, sigma);
+        k_large_ab64<<<pl.grid_ab64, SIGMA_THREADS, pl.smem_ab64, ctx->stream>>>(pl.L, (const double *)c, sigma,
+                                                                                   sgn);
     } else {
         // the dense product on the tensor cores (large_tc.cu)
         const int rc = large_ab_tc(ctx->stream, ctx->sm_count, ctx->smem_optin, pl.L.P, pl.L.Ns, pl.L.R, pl.L.tab,
@@ -662,11 +710,21 @@ static int large_sigma_launch(mbe_ctx *ctx, const LargePlan &pl, const T *c, dou
     }
     const int grid_ss = sizeof(T) == 8 ? pl.grid_ss64 : pl.grid_ss32;
     const size_t smem_ss = sizeof(T) == 8 ? pl.smem_ss64 : pl.smem_ss32;
-    k_large_ss<T, false><<<grid_ss, SS_THREADS, smem_ss, ctx->stream>>>(pl.L, c, sigma);
-    k_large_transpose<T><<<pl.grid_tr, dim3(32, 8), 0, ctx->stream>>>(c, Ns, cT);
-    k_large_ss<T, true><<<grid_ss, SS_THREADS, smem_ss, ctx->stream>>>(pl.L, cT, sigma);
+    if (sgn == 0) {
+        T *cT = (T *)pl.cT;
+        k_large_ss<T, false><<<grid_ss, SS_THREADS, smem_ss, ctx->stream>>>(pl.L, c, sigma);
+        k_large_transpose<T><<<pl.grid_tr, dim3(32, 8), 0, ctx->stream>>>(c, Ns, cT);
+        k_large_ss<T, true><<<grid_ss, SS_THREADS, smem_ss, ctx->stream>>>(pl.L, cT, sigma);
+    } else {
+        // c in the sector sgn: the beta same-spin term is sgn times the transpose
+        // of the alpha one, so one product (into the spare buffer) and a
+        // transposing add replace the second product and the transpose of c
+        double *A = (double *)pl.cT;
+        k_large_ss<T, false, true><<<grid_ss, SS_THREADS, smem_ss, ctx->stream>>>(pl.L, c, A);
+        k_sym_add<<<pl.grid_tr, dim3(32, 8), 0, ctx->stream>>>(A, Ns, sgn, sigma);
+    }
     MBE_CU(cudaGetLastError());
-    ctx->launches += 4;
+    ctx->launches += sgn == 0 ? 4 : 3;
     return tl.done();
 }
 
@@ -819,12 +877,13 @@ static void dot_to(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, const d
 }
 
 template <typename T>
-static int large_apply(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, const double *vin, double *wout)
+static int large_apply(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, const double *vin, double *wout,
+                       int sgn)
 {
-    if (sizeof(T) == 8) return large_sigma_launch<double>(ctx, pl, vin, wout, pl.L.n);
+    if (sizeof(T) == 8) return large_sigma_launch<double>(ctx, pl, vin, wout, pl.L.n, sgn);
     k_to_float<<<pl.grid_vec, 256, 0, ctx->stream>>>(vin, pl.L.N, D.c32);
     ++ctx->launches;
-    return large_sigma_launch<float>(ctx, pl, D.c32, wout, pl.L.n);
+    return large_sigma_launch<float>(ctx, pl, D.c32, wout, pl.L.n, sgn);
 }
 
 // One Davidson phase on the large space (T = sigma arithmetic).  D.x: start
@@ -856,7 +915,7 @@ static int large_phase(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, int
     k_scale_copy<<<g, 256, 0, st>>>(D.x, nullptr, D.dots, N, D.V, nullptr, nullptr);
     ctx->launches += 2;
     if (anch) {
-        if ((rc = large_sigma_launch<double>(ctx, pl, D.V, D.W, pl.L.n))) return rc;
+        if ((rc = large_sigma_launch<double>(ctx, pl, D.V, D.W, pl.L.n, sgn))) return rc;
         ++*nsig64;
         k_project_sector<<<g, 256, 0, st>>>(D.W, Ns, sgn, N);
         ++ctx->launches;
@@ -866,7 +925,7 @@ static int large_phase(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, int
         k_shift_image<<<g, 256, 0, st>>>(D.V, shift, N, D.W);
         ++ctx->launches;
     } else {
-        if ((rc = large_apply<T>(ctx, pl, D, D.V, D.W))) return rc;
+        if ((rc = large_apply<T>(ctx, pl, D, D.V, D.W, sgn))) return rc;
         ++*nsig;
     }
     k_project_sector<<<g, 256, 0, st>>>(D.W, Ns, sgn, N);
@@ -987,7 +1046,7 @@ static int large_phase(mbe_ctx *ctx, const LargePlan &pl, const LargeDav &D, int
         }
         k_scale_copy<<<g, 256, 0, st>>>(u, nullptr, D.dots, N, u, nullptr, nullptr);
         ++ctx->launches;
-        if ((rc = large_apply<T>(ctx, pl, D, u, D.W + (size_t)m * ld))) return rc;
+        if ((rc = large_apply<T>(ctx, pl, D, u, D.W + (size_t)m * ld, sgn))) return rc;
         ++*nsig;
         k_project_sector<<<g, 256, 0, st>>>(D.W + (size_t)m * ld, Ns, sgn, N);
         ++ctx->launches;
