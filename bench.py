@@ -750,10 +750,13 @@ def run_molecule(args):
     import paper_1910_03527_gb300 as eng
     from workloads import workload
 
+    import numpy as np
+
     eng.build()
     w = workload("molecule40")
     dev = torch.device("cuda", 0)
     ctx = eng.Context(0)
+    measure_peaks(ctx)
     th1, teri, tocc = (torch.tensor(x, device=dev) for x in (w.h1, w.eri, w.occ))
     occ_h = [int(v) for v in w.occ]
     orders = list(range(1, args.molecule_max_order + 1))
@@ -775,14 +778,38 @@ def run_molecule(args):
         recs = ctx.take_timings()
         ctx.set_timing(False)
         per_order = {}
+        occ_np = np.asarray(w.occ)
         for i, n in enumerate(orders):
             ms = sum(r[3] for r in recs if r[0] == n)
             nt = int(res["tuples"][i].shape[0])
             it = res["iters"][i]
+            # sigma flops of the order's solves (half space: Ns(Ns+1)/2 elements per
+            # product), float64 and float32, over the summed solver-launch time; the
+            # Davidson subspace algebra is not counted, so this is a lower bound
+            roof = None
+            if nt and ms > 0:
+                tup = res["tuples"][i].cpu().numpy()
+                its = it.cpu().numpy()
+                kk = occ_np[tup].sum(axis=1) + int(occ_np[w.ref].sum())
+                ncas = len(w.ref) + n
+                f64 = f32 = 0.0
+                for k in np.unique(kk):
+                    sel = kk == k
+                    ns = math.comb(ncas, int(k))
+                    per = sigma_flops_per_det(ncas, int(k)) * (ns * (ns + 1) // 2)
+                    f64 += float(((its[sel] >> 16) & 0xffff).sum()) * per
+                    f32 += float((its[sel] & 0xffff).sum()) * per
+                t_s = ms / 1e3
+                ach = (f64 + f32 * PEAKS["fp64"] / PEAKS["fp32"]) / t_s / 1e12
+                roof = {"bound": "alu", "kernel": "k_casci_block (+ warp-solver launches of the order)",
+                        "fp64_tflops": f64 / t_s / 1e12, "fp32_tflops": f32 / t_s / 1e12,
+                        "achieved_fp64_equivalent": ach, "frac_of_measured": ach / PEAKS["fp64"],
+                        "counted": "sigma products only (lower bound)"}
             per_order[n] = {"tuples": nt, "solver_ms": ms, "solves_per_s": nt / (ms / 1e3) if ms > 0 else None,
                             "fp64_sigma_per_tuple": float(((it >> 16) & 0xffff).double().mean().item()) if nt else 0,
                             "fp32_sigma_per_tuple": float((it & 0xffff).double().mean().item()) if nt else 0,
-                            "non_ok": int(((res["status"][i] >= 1) & (res["status"][i] <= 3)).sum().item())}
+                            "non_ok": int(((res["status"][i] >= 1) & (res["status"][i] <= 3)).sum().item()),
+                            "roofline": roof}
         n_t = sum(v["tuples"] for v in per_order.values())
         out["per_precision"][prec] = {"value": n_t / t, "seconds": t, "e_total": e_tot, "per_order": per_order}
     print(json.dumps(out))
