@@ -192,9 +192,11 @@ __global__ void k_large_diag(LargeCas L)
 //     sigma[Ia][Ib] = sum_{x in list(Ia)} s_x sum_{y in list(Ib)} s_y V[p_x][p_y] c[J_x][J_y]
 // (written, not accumulated). The beta lists are read through the transposed
 // table, so a warp's 32 consecutive Ib load 32 consecutive words.
-// sgn = +1 or -1: c lies in that spin-flip sector (c[Ia][Ib] = sgn c[Ib][Ia]), so
-// only the elements with Ia <= Ib are computed and each is mirrored, sigma[Ib][Ia]
-// = sgn sigma[Ia][Ib] (the diagonal of the odd sector vanishes); 0: every element.
+// SECTOR: c lies in the spin-flip sector sgn (c[Ia][Ib] = sgn c[Ib][Ia]), so only
+// the elements with Ia <= Ib are computed, walking the upper triangle row by
+// row, and each is mirrored, sigma[Ib][Ia] = sgn sigma[Ia][Ib] (the diagonal of
+// the odd sector vanishes).  Otherwise every element, in row-major order.
+template <bool SECTOR>
 __global__ void __launch_bounds__(SIGMA_THREADS) k_large_ab64(LargeCas L, const double *__restrict__ c,
                                                                double *__restrict__ sigma, int sgn)
 {
@@ -203,12 +205,24 @@ __global__ void __launch_bounds__(SIGMA_THREADS) k_large_ab64(LargeCas L, const 
     const int P = L.P, Ns = L.Ns, R = L.R;
     for (int e = threadIdx.x; e < P * P; e += blockDim.x) Vs[e] = L.V[e];
     __syncthreads();
-    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < L.N; d += (int64_t)gridDim.x * blockDim.x) {
-        const int ia = (int)(d / Ns), ib = (int)(d - (int64_t)ia * Ns);
-        if (sgn != 0 && ia > ib) continue;
-        if (sgn < 0 && ia == ib) {
-            sigma[d] = 0.0;
-            continue;
+    const int64_t count = SECTOR ? (int64_t)Ns * (Ns + 1) / 2 : L.N;
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < count; h += (int64_t)gridDim.x * blockDim.x) {
+        int ia, ib;
+        if (SECTOR) {
+            // row ia of the upper triangle starts at ia Ns - ia (ia - 1) / 2
+            const double b2 = 2.0 * Ns + 1.0;
+            ia = (int)((b2 - sqrt(b2 * b2 - 8.0 * (double)h)) * 0.5);
+            auto start = [&](int64_t r) { return r * Ns - r * (r - 1) / 2; };
+            while (ia > 0 && start(ia) > h) --ia;
+            while (ia + 1 < Ns && start(ia + 1) <= h) ++ia;
+            ib = ia + (int)(h - start(ia));
+            if (sgn < 0 && ia == ib) {
+                sigma[(int64_t)ia * Ns + ib] = 0.0;
+                continue;
+            }
+        } else {
+            ia = (int)(h / Ns);
+            ib = (int)(h - (int64_t)ia * Ns);
         }
         double acc0 = 0.0, acc1 = 0.0;
         const int32_t *ta = L.tab + (size_t)ia * R;
@@ -231,8 +245,9 @@ __global__ void __launch_bounds__(SIGMA_THREADS) k_large_ab64(LargeCas L, const 
             const double s = s0 + s1;
             if (x & 1) acc1 += flip_if(s, entry_neg(ea)); else acc0 += flip_if(s, entry_neg(ea));
         }
-        sigma[d] = acc0 + acc1;
-        if (sgn != 0 && ia < ib) sigma[(int64_t)ib * Ns + ia] = sgn > 0 ? acc0 + acc1 : -(acc0 + acc1);
+        const double v = acc0 + acc1;
+        sigma[(int64_t)ia * Ns + ib] = v;
+        if (SECTOR && ia < ib) sigma[(int64_t)ib * Ns + ia] = sgn > 0 ? v : -v;
     }
 }
 
@@ -655,9 +670,10 @@ static int large_setup(mbe_ctx *ctx, int norb, const double *h1, const double *e
     plan->smem_ab64 = (size_t)P * P * 8;
     MBE_CHECK(plan->smem_ab64 <= ctx->smem_optin, MBE_EUNSUPPORTED, "large CASCI: V needs %zu B shared memory",
               plan->smem_ab64);
-    MBE_CU(cudaFuncSetAttribute(k_large_ab64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem_ab64));
+    MBE_CU(cudaFuncSetAttribute(k_large_ab64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem_ab64));
+    MBE_CU(cudaFuncSetAttribute(k_large_ab64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem_ab64));
     int b = 0;
-    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_large_ab64, SIGMA_THREADS, plan->smem_ab64));
+    MBE_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_large_ab64<false>, SIGMA_THREADS, plan->smem_ab64));
     plan->grid_ab64 = ctx->sm_count * (b > 0 ? b : 1);
     plan->smem_ss64 = (size_t)SS_ROWS * (SS_TK + 1) * 8;
     plan->smem_ss32 = (size_t)SS_ROWS * (SS_TK + 1) * 4;
@@ -700,8 +716,12 @@ static int large_sigma_launch(mbe_ctx *ctx, const LargePlan &pl, const T *c, dou
     TimedLaunch tl(ctx, order_tag, 2, sizeof(T) == 8 ? 64 : 32);
     const int Ns = pl.L.Ns;
     if (sizeof(T) == 8) {
-        k_large_ab64<<<pl.grid_ab64, SIGMA_THREADS, pl.smem_ab64, ctx->stream>>>(pl.L, (const double *)c, sigma,
-                                                                                   sgn);
+        if (sgn == 0)
+            k_large_ab64<false><<<pl.grid_ab64, SIGMA_THREADS, pl.smem_ab64, ctx->stream>>>(pl.L, (const double *)c,
+                                                                                          sigma, 0);
+        else
+            k_large_ab64<true><<<pl.grid_ab64, SIGMA_THREADS, pl.smem_ab64, ctx->stream>>>(pl.L, (const double *)c,
+                                                                                         sigma, sgn);
     } else {
         // the dense product on the tensor cores (large_tc.cu)
         const int rc = large_ab_tc(ctx->stream, ctx->sm_count, ctx->smem_optin, pl.L.P, pl.L.Ns, pl.L.R, pl.L.tab,
