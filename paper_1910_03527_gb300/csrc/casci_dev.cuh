@@ -39,7 +39,6 @@ namespace mbe {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int WARP_MAX_N = 8;
-constexpr int WARP_MAX_NDET = 416;  // determinants one warp holds (13 per lane); mbe_tuning's upper limit
 constexpr int WARPS_PER_BLOCK = 4;
 constexpr int CTA_THREADS = 256;
 constexpr int MAX_BUCKETS = 8;

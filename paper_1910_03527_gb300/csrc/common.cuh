@@ -31,6 +31,10 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
         }                                       \
     } while (0)
 
+// Determinants one warp of the warp solver holds (13 per lane): the upper limit
+// of mbe_tuning.warp_max_ndet and its default.
+inline constexpr int WARP_MAX_NDET = 416;
+
 // ------------------------------------------------------------------ combinatorics
 
 __host__ __device__ inline int64_t binom(int n, int k)

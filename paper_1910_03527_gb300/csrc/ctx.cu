@@ -157,7 +157,7 @@ int mbe_ctx_create(mbe_ctx **ctx, int device, void *cuda_stream)
     c->sm_count = prop.multiProcessorCount;
     c->smem_optin = prop.sharedMemPerBlockOptin;
     for (auto &row : c->tune)
-        for (auto &t : row) t = mbe_tuning{416, 4, 20};
+        for (auto &t : row) t = mbe_tuning{WARP_MAX_NDET, 4, 20};
     e = cudaMalloc(&c->dev_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->dev_err, 0, sizeof(int));
     if (e != cudaSuccess) {
@@ -175,7 +175,7 @@ int mbe_ctx_set_tuning(mbe_ctx *ctx, int precision, int n_cas, const mbe_tuning 
     MBE_CHECK(precision == MBE_PREC_FP64 || precision == MBE_PREC_MIXED, MBE_EINVAL,
               "mbe_ctx_set_tuning: precision %d", precision);
     MBE_CHECK(n_cas >= 0 && n_cas <= MBE_MAX_CAS, MBE_EINVAL, "mbe_ctx_set_tuning: n_cas %d", n_cas);
-    MBE_CHECK(t->warp_max_ndet >= 1 && t->warp_max_ndet <= 416 && t->warp_warps >= 1 && t->warp_warps <= 4 &&
+    MBE_CHECK(t->warp_max_ndet >= 1 && t->warp_max_ndet <= WARP_MAX_NDET && t->warp_warps >= 1 && t->warp_warps <= 4 &&
                   t->block_basis >= 4 && t->block_basis <= 20,
               MBE_EINVAL, "mbe_ctx_set_tuning: values out of range (%d, %d, %d)", t->warp_max_ndet, t->warp_warps,
               t->block_basis);
