@@ -124,6 +124,9 @@ __global__ void __launch_bounds__(CTA_THREADS, 2) k_casci_block(BatchArgs a, int
         double lam = 0.0;
         int status = MBE_STATUS_OK, n64 = 0, n32 = 0;
         bool degen = false;
+        // one copy of the sector's Davidson: two inlined copies, both hot on an SM,
+        // overflow the instruction cache and slow every phase of every warp
+#pragma unroll 1
         for (int sector = 0; sector < 2; ++sector) {
             if (sector == 1 && (pb.Ns < 2 || status != MBE_STATUS_OK || a.even_only)) break;
             const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};

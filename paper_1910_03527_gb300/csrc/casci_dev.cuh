@@ -1153,6 +1153,9 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
             int status = MBE_STATUS_OK, n64 = 0, n32 = 0;
             bool degen = false;
             if constexpr (MODE == WM_F64) n32 = a.pstate[2 * t + 1];  // the mixed solver's float32 work
+            // one copy of the sector's Davidson: two inlined copies, both hot on an SM,
+            // overflow the instruction cache and slow every phase of every warp
+#pragma unroll 1
             for (int sector = 0; sector < 2; ++sector) {
                 if (sector == 1 && (pb.Ns < 2 || status != MBE_STATUS_OK || a.even_only)) break;
                 const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
@@ -1570,6 +1573,9 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, DPL <= 8 ? 4 : 3)
         int n32 = 0, n64 = 0;
         bool redo = false, degen = false;
         double lam = 0.0, lam32 = 0.0;
+        // one copy of the sector's Davidson: two inlined copies, both hot on an SM,
+        // overflow the instruction cache and slow every phase of every warp
+#pragma unroll 1
         for (int sector = 0; sector < 2 && !redo; ++sector) {
             if (sector == 1 && (pb.Ns < 2 || a.even_only)) break;
             const SectorGuess sg{sector == 0 ? bi : bj, sector == 0 ? 1 : -1};
