@@ -43,6 +43,11 @@ constexpr int WARPS_PER_BLOCK = 4;
 constexpr int CTA_THREADS = 256;
 constexpr int MAX_BUCKETS = 8;
 constexpr int DPL_SET[5] = {1, 2, 4, 8, 13};
+// The warp solvers keep their float32 V with both signs, V2[x][2y + s] =
+// (-1)^s V[x][y]: the low 9 bits of a replacement-list entry (pair << 1 | neg)
+// then index the signed value directly, which saves the pair decode and the
+// sign flip in the innermost loop of the float32 sigma.
+constexpr bool V32_SIGNED = true;
 
 struct ClassInfo {
     const uint32_t *strings;
@@ -200,7 +205,7 @@ __device__ inline bool build_A(const BatchArgs &a, int64_t t, int *A)
 
 // a2 + a4 set-up shared by both solvers.  Fills h_eff, V, h', Hs and the diagonal.
 template <class G>
-__device__ void setup_problem(const BatchArgs &a, Problem &pb, bool want32)
+__device__ void setup_problem(const BatchArgs &a, Problem &pb, bool want32, bool signed32 = false)
 {
     const int tid = G::rank(), nt = G::size();
     const int n = pb.n, P = pb.P, norb = a.norb;
@@ -230,7 +235,12 @@ __device__ void setup_problem(const BatchArgs &a, Problem &pb, bool want32)
         int p = pb.pp[2 * x], q = pb.pp[2 * x + 1], r = pb.pp[2 * y], s = pb.pp[2 * y + 1];
         double v = a.eri[eri_index(norb, pb.A[p], pb.A[q], pb.A[r], pb.A[s])];
         pb.V64[e] = v;
-        if (want32) pb.V32[e] = (float)v;
+        if (want32 && signed32) {
+            pb.V32[x * 2 * P + 2 * y] = (float)v;
+            pb.V32[x * 2 * P + 2 * y + 1] = -(float)v;
+        } else if (want32) {
+            pb.V32[e] = (float)v;
+        }
     }
     G::sync();
     // h'_pq = h_eff_pq - 1/2 sum_r (pr|rq)
@@ -348,7 +358,8 @@ __device__ __noinline__ void add_s2_half(const Problem &pb, const TV *__restrict
     }
 }
 
-template <typename T, typename TV = T>
+// S2: V is the signed doubled table [P][2P] (V32_SIGNED), else the plain [P][P].
+template <typename T, typename TV = T, bool S2 = false>
 __device__ inline T sigma_elem(const Problem &pb, const T *__restrict__ V, const T *__restrict__ Hs,
                                const TV *__restrict__ c, int d)
 {
@@ -368,18 +379,31 @@ __device__ inline T sigma_elem(const Problem &pb, const T *__restrict__ V, const
     const int R = pb.R;
     for (int x = 0; x < R; ++x) {
         int ea = ta[x];
-        const T *vrow = V + entry_pair(ea) * pb.P;
         const TV *cr = c + entry_J(ea) * Ns;
         T s0 = 0, s1 = 0;
         int y = 0;
-        for (; y + 1 < R; y += 2) {
-            int e0 = tb[y], e1 = tb[y + 1];
-            s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), (T)cr[entry_J(e0)], s0);
-            s1 = fma(flip_if(vrow[entry_pair(e1)], entry_neg(e1)), (T)cr[entry_J(e1)], s1);
-        }
-        if (y < R) {
-            int e0 = tb[y];
-            s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), (T)cr[entry_J(e0)], s0);
+        if constexpr (S2) {
+            const T *vrow = V + entry_pair(ea) * (2 * pb.P);
+            for (; y + 1 < R; y += 2) {
+                int e0 = tb[y], e1 = tb[y + 1];
+                s0 = fma(vrow[e0 & 0x1ff], (T)cr[entry_J(e0)], s0);
+                s1 = fma(vrow[e1 & 0x1ff], (T)cr[entry_J(e1)], s1);
+            }
+            if (y < R) {
+                int e0 = tb[y];
+                s0 = fma(vrow[e0 & 0x1ff], (T)cr[entry_J(e0)], s0);
+            }
+        } else {
+            const T *vrow = V + entry_pair(ea) * pb.P;
+            for (; y + 1 < R; y += 2) {
+                int e0 = tb[y], e1 = tb[y + 1];
+                s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), (T)cr[entry_J(e0)], s0);
+                s1 = fma(flip_if(vrow[entry_pair(e1)], entry_neg(e1)), (T)cr[entry_J(e1)], s1);
+            }
+            if (y < R) {
+                int e0 = tb[y];
+                s0 = fma(flip_if(vrow[entry_pair(e0)], entry_neg(e0)), (T)cr[entry_J(e0)], s0);
+            }
         }
         T s = s0 + s1;
         if (x & 1) acc1 += flip_if(s, entry_neg(ea)); else acc0 += flip_if(s, entry_neg(ea));
@@ -654,7 +678,8 @@ __device__ inline void sigma_warp(const Problem &pb, const T *V, const T *Hs, co
 #pragma unroll 1
     for (int h = lane; h < nh; h += 32) {
         const int d = ia * Ns + ib, pd = ib * Ns + ia;
-        const T v = (pb.sector < 0 && ia == ib) ? (T)0 : sigma_elem<T, TV>(pb, V, Hs, c, d);
+        const T v = (pb.sector < 0 && ia == ib) ? (T)0
+                                                   : sigma_elem<T, TV, V32_SIGNED && sizeof(T) == 4>(pb, V, Hs, c, d);
         sbuf[d] = v;
         if (pd != d) sbuf[pd] = pb.sector > 0 ? v : -v;
         tri_advance(ia, ib, 32, Ns);
@@ -967,7 +992,7 @@ __host__ __device__ inline WarpLayout warp_layout(int n, int ns, int r, int N, b
     L.off_h = o; o = al16(o + 8 * n * n);
     L.off_hp = o; o = al16(o + 8 * P);
     L.off_V64 = o; o = al16(o + 8 * P * P);
-    L.off_V32 = o; o = al16(o + 4 * P * P);
+    L.off_V32 = o; o = al16(o + (V32_SIGNED ? 8 : 4) * P * P);
     L.off_Hs64 = o; o = al16(o + 8 * ns * HSS);
     L.off_Hs32 = o; o = al16(o + 4 * ns * HSS);
     L.off_diag = o; o = al16(o + 8 * N);
@@ -1103,7 +1128,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32)
         __syncwarp();
         const bool mixed = a.precision == MBE_PREC_MIXED;
         pb.s2mu = a.s2mu;
-        setup_problem<WarpGroup>(a, pb, mixed);
+        setup_problem<WarpGroup>(a, pb, mixed, V32_SIGNED);
         // Phi_A: the in-space occupied orbitals
         uint32_t mphi = 0;
         for (int i = 0; i < n; ++i)
@@ -1347,7 +1372,7 @@ __host__ __device__ inline MixLayout mix_layout(int n, int ns, int r, int N)
     L.off_A = o; o = al16(o + 4 * MBE_MAX_CAS);
     L.off_pp = o; o = al16(o + 4 * P);
     L.off_Vp = o; o = al16(o + 8 * (P * (P + 1) / 2));
-    L.off_V32 = o; o = al16(o + 4 * P * P);
+    L.off_V32 = o; o = al16(o + (V32_SIGNED ? 8 : 4) * P * P);
     L.off_Hsp = o; o = al16(o + 8 * (ns * (ns + 1) / 2));
     L.off_Hs32 = o; o = al16(o + 4 * ns * HSS);
     L.off_diag = o; o = al16(o + 4 * N);
@@ -1403,7 +1428,12 @@ static __device__ void setup_mix(const BatchArgs &a, Problem &pb, char *ws, cons
         const int x = e / P, y = e - x * P;
         const int p = pp[2 * x], q = pp[2 * x + 1], r = pp[2 * y], s = pp[2 * y + 1];
         const double v = a.eri[eri_index(norb, pb.A[p], pb.A[q], pb.A[r], pb.A[s])];
-        pb.V32[e] = (float)v;
+        if (V32_SIGNED) {
+            pb.V32[x * 2 * P + 2 * y] = (float)v;
+            pb.V32[x * 2 * P + 2 * y + 1] = -(float)v;
+        } else {
+            pb.V32[e] = (float)v;
+        }
         if (x >= y) Vp[tri_index(x, y)] = v;
     }
     __syncwarp();
