@@ -411,6 +411,54 @@ __device__ inline T sigma_elem(const Problem &pb, const T *__restrict__ V, const
     return acc0 + acc1;
 }
 
+// a5: one sigma element of the block solver's float32 phase, the same terms as
+// sigma_elem in another loop order.  The block's neighbouring threads hold
+// neighbouring beta strings of one alpha string, so the alpha string's
+// replacement list runs innermost (one table entry for the whole warp per step,
+// the vector read within one row of c), and the beta-beta term reads Hs[J][Ib]
+// for Hs[Ib][J] (Hs is symmetric), so that neighbouring threads read
+// neighbouring elements.  Measured on 9-orbital tuples: the float32 phase 10%
+// faster than with sigma_elem; the float64 sigma, bound by the FP64 pipe,
+// keeps sigma_elem (it was 2% slower in this order).
+template <typename T>
+__device__ inline T sigma_elem_ashared(const Problem &pb, const T *__restrict__ V, const T *__restrict__ Hs,
+                                       const T *__restrict__ c, int ia, int ib)
+{
+    const int Ns = pb.Ns, HSS = pb.HSS, P = pb.P;
+    const T *ha = Hs + ia * HSS;
+    const T *crow = c + ia * Ns;
+    T acc0 = 0, acc1 = 0;
+    for (int J = 0; J < Ns; ++J) {
+        acc0 = fma(ha[J], c[J * Ns + ib], acc0);
+        acc1 = fma(Hs[J * HSS + ib], crow[J], acc1);
+    }
+    const int32_t *ta = pb.tab + ia * pb.RS;
+    const int32_t *tb = pb.tab + ib * pb.RS;
+    const int R = pb.R;
+    for (int y = 0; y < R; ++y) {
+        const int eb = tb[y];
+        const T *vcol = V + entry_pair(eb);  // column pair(eb) of V, stride P
+        const T *ccol = c + entry_J(eb);     // column J_b of c, stride Ns
+        // four independent chains keep four gathers of c in flight
+        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        int x = 0;
+        for (; x + 3 < R; x += 4) {
+            const int e0 = ta[x], e1 = ta[x + 1], e2 = ta[x + 2], e3 = ta[x + 3];
+            s0 = fma(flip_if(vcol[entry_pair(e0) * P], entry_neg(e0)), ccol[entry_J(e0) * Ns], s0);
+            s1 = fma(flip_if(vcol[entry_pair(e1) * P], entry_neg(e1)), ccol[entry_J(e1) * Ns], s1);
+            s2 = fma(flip_if(vcol[entry_pair(e2) * P], entry_neg(e2)), ccol[entry_J(e2) * Ns], s2);
+            s3 = fma(flip_if(vcol[entry_pair(e3) * P], entry_neg(e3)), ccol[entry_J(e3) * Ns], s3);
+        }
+        for (; x < R; ++x) {
+            const int e0 = ta[x];
+            s0 = fma(flip_if(vcol[entry_pair(e0) * P], entry_neg(e0)), ccol[entry_J(e0) * Ns], s0);
+        }
+        const T s = (s0 + s1) + (s2 + s3);
+        if (y & 1) acc1 += flip_if(s, entry_neg(eb)); else acc0 += flip_if(s, entry_neg(eb));
+    }
+    return acc0 + acc1;
+}
+
 // Lowest eigenpair of the symmetric 3x3 Rayleigh-Ritz matrix G (m = 2 or 3 active
 // rows; with m = 2 the middle row/column is absent).  Float32 Jacobi on G shifted
 // by G00, then (float64 phase) one inverse-iteration step in float64.
@@ -1961,7 +2009,11 @@ __device__ inline void sigma_block(const Problem &pb, const T *Vi, const T *Hs, 
     tri_advance(ia, ib, threadIdx.x, Ns);
     for (int h = threadIdx.x; h < nh; h += blockDim.x) {
         const int d = ia * Ns + ib, pd = ib * Ns + ia;
-        const T v = (pb.sector < 0 && ia == ib) ? (T)0 : sigma_elem<T>(pb, Vi, Hs, src, d);
+        T v = (T)0;
+        if (!(pb.sector < 0 && ia == ib)) {
+            if constexpr (sizeof(T) == 4) v = sigma_elem_ashared<T>(pb, Vi, Hs, src, ia, ib);
+            else v = sigma_elem<T>(pb, Vi, Hs, src, d);
+        }
         dst[d] = v;
         if (pd != d) dst[pd] = pb.sector > 0 ? v : -v;
         tri_advance(ia, ib, blockDim.x, Ns);
