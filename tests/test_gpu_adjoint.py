@@ -3,7 +3,9 @@
 Checked against the oracle adjoint (weights and full gradients on small
 systems), against central finite differences of GPU energies on the L=46
 Hubbard ring (dE/dt, dE/dU) and on the 20-orbital molecule (dE/dh_pq and
-dE/d(pq|rs) symmetry orbits), and against the exact Hubbard homogeneity
+dE/d(pq|rs) symmetry orbits at orders 1-2; directional derivatives over 50
+random integral entries and over all of them at orders 1-3), and against the
+exact Hubbard homogeneity
 t dE/dt + U dE/dU = E and trace(gamma) = N.
 """
 
@@ -165,3 +167,69 @@ def test_molecule20_gradient_finite_differences(eng, ctx):
         fd = (energy(w.h1, ep) - energy(w.h1, em)) / (2 * d)
         want = sum(ge[o] for o in orbit)
         assert abs(fd - want) < 1e-6 * max(1.0, abs(want)), ("eri", idx, fd, want)
+
+
+def _symmetric_h_direction(rng, n, entries):
+    """Random symmetric one-body direction on `entries` random (p, q) pairs."""
+    D = np.zeros((n, n))
+    for _ in range(entries):
+        p, q = (int(x) for x in rng.integers(0, n, size=2))
+        D[p, q] = D[q, p] = rng.normal()
+    return D
+
+
+def _symmetric_eri_direction(rng, n, orbits):
+    """Random direction with the 8-fold symmetry of (pq|rs) on `orbits` random orbits."""
+    D = np.zeros((n,) * 4)
+    for _ in range(orbits):
+        v = rng.normal()
+        for o in _orbit(*(int(x) for x in rng.integers(0, n, size=4))):
+            D[o] = v
+    return D
+
+
+def test_molecule20_directional_derivatives_orders_1_3(eng, ctx):
+    # Directional derivatives of the orders 1-3 MBE energy of the 20-orbital
+    # molecule (364 order-3 tuples of 9 orbitals, 15,876 determinants, block
+    # solver): dE along D = sum_pq dE/dh_pq D_pq + sum_pqrs dE/d(pq|rs) D_pqrs
+    # from the adjoint, against the central difference of two GPU energies.
+    # Three directions: 25 random one-body entries, 25 random two-electron
+    # symmetry orbits (50 integral entries in all), and a dense direction over
+    # every entry of both; each is scaled to unit norm.
+    directional_check(eng, ctx, [1, 2, 3])
+
+
+def directional_check(eng, ctx, orders):
+    w = workload("molecule20")
+    opts = eng.Opts(tol=1e-9)
+    occ_d = dev(w.occ)
+
+    def energy(h, e):
+        out = eng.run_mbe(ctx, dev(h), dev(e), occ_d, w.ref, w.exp, orders, w.skip, opts,
+                          occ_host=w.occ.tolist())
+        assert all(bool((s == 0).all()) for s in out["status"])
+        return float(out["e_total"].item())
+
+    gh, ge, fwd = eng.mbe_gradient(ctx, dev(w.h1), dev(w.eri), occ_d, w.ref, w.exp, orders, w.skip, opts,
+                                   occ_host=w.occ.tolist())
+    assert all(bool((s == 0).all()) for s in fwd["status"])
+    gh, ge = gh.cpu().numpy(), ge.cpu().numpy()
+    n = w.h1.shape[0]
+    rng = np.random.default_rng(2020)
+    dense_h = rng.normal(size=(n, n))
+    dense_e = rng.normal(size=(n,) * 4)
+    dense_e = sum(np.transpose(dense_e, p) for p in
+                  [(0, 1, 2, 3), (1, 0, 2, 3), (0, 1, 3, 2), (1, 0, 3, 2),
+                   (2, 3, 0, 1), (3, 2, 0, 1), (2, 3, 1, 0), (3, 2, 1, 0)]) / 8.0
+    directions = {
+        "h entries": (_symmetric_h_direction(rng, n, 25), np.zeros((n,) * 4)),
+        "eri orbits": (np.zeros((n, n)), _symmetric_eri_direction(rng, n, 25)),
+        "dense": ((dense_h + dense_h.T) / 2.0, dense_e),
+    }
+    d = 1e-4
+    for name, (Dh, De) in directions.items():
+        norm = math.sqrt(float((Dh * Dh).sum() + (De * De).sum()))
+        Dh, De = Dh / norm, De / norm
+        want = float((gh * Dh).sum() + (ge * De).sum())
+        fd = (energy(w.h1 + d * Dh, w.eri + d * De) - energy(w.h1 - d * Dh, w.eri - d * De)) / (2 * d)
+        assert abs(fd - want) < 1e-6 * max(1.0, abs(want)), (name, fd, want)
