@@ -128,7 +128,8 @@ int mbe_ctx_create(mbe_ctx **ctx, int device, void *cuda_stream);
 /* Changes the stream later calls issue work on.  Host only. */
 int mbe_ctx_set_stream(mbe_ctx *ctx, void *cuda_stream);
 
-/* Waits for all work of the context, frees its workspace and the context. */
+/* Waits for all work of the context, frees its workspace, its worker contexts
+   (casci_batch_routed) and the context. */
 void mbe_ctx_destroy(mbe_ctx *ctx);
 
 /* Text of the last error raised by a call on this thread (never NULL). */
@@ -452,9 +453,16 @@ int casci_solve(mbe_ctx *ctx, int norb, const double *h1, const double *eri, con
  *                casci_batch itself.
  * A routed tuple's iters_out holds casci_solve's sigma counts in the casci_batch
  * encoding; a routed active space with one determinant (Phi_A) gets eps =
- * -e_ref_corr without a solve.  Synchronous when any tuple is routed (the host
- * reads the tuples and occupations, and casci_solve is synchronous); temporary
- * device buffers are stream-ordered allocations freed before return.
+ * -e_ref_corr without a solve.  Routed tuples of up to 4,000,000 determinants
+ * are solved four at a time, each on a worker context of ctx (its own
+ * non-blocking stream and host thread), after the work already queued on ctx's
+ * stream; a solve that size leaves most of the GPU idle while its host loop
+ * waits for each iteration's scalars.  The worker contexts (streams, workspaces,
+ * string tables) are created on first use and freed by mbe_ctx_destroy; the
+ * results do not depend on which worker solved a tuple.  Synchronous when any
+ * tuple is routed (the host reads the tuples and occupations, and casci_solve
+ * is synchronous); temporary device buffers are stream-ordered allocations
+ * freed before return.
  * Errors: as casci_batch and casci_solve; MBE_EUNSUPPORTED for |R| + order
  * above MBE_MAX_LARGE_CAS.  A malformed routed tuple gets MBE_STATUS_BADINPUT
  * and eps NaN, as in casci_batch.

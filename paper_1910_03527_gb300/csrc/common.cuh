@@ -110,6 +110,10 @@ struct mbe_ctx {
         cudaEvent_t start, stop;
     };
     std::vector<Pending> pending;
+    // worker contexts of casci_batch_routed, each on its own non-blocking stream
+    // (created on first use, destroyed with this context)
+    std::vector<mbe_ctx *> workers;
+    std::vector<cudaStream_t> worker_streams;
 };
 
 namespace mbe {

@@ -214,6 +214,10 @@ int mbe_ctx_sync(mbe_ctx *ctx)
 void mbe_ctx_destroy(mbe_ctx *ctx)
 {
     if (!ctx) return;
+    for (size_t i = 0; i < ctx->workers.size(); ++i) {
+        mbe_ctx_destroy(ctx->workers[i]);
+        cudaStreamDestroy(ctx->worker_streams[i]);
+    }
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->ws) cudaFreeAsync(ctx->ws, ctx->stream);

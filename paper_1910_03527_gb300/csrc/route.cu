@@ -7,7 +7,10 @@
 // solved by casci_solve with the whole GPU.  Both write eps = E_CAS(R u Omega) -
 // E_Phi - E_ref,corr (Eq. 1), so the routed results are interchangeable.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -38,6 +41,33 @@ __global__ void k_route_direct(int64_t n, const int64_t *rows, const int32_t *st
     eps_out[r] = status[i] == MBE_STATUS_BADINPUT ? (double)NAN : -e_ref_corr;
     status_out[r] = status[i];
     if (iters_out) iters_out[r] = 0;
+}
+
+// Whole-GPU solves of up to ROUTE_CONCURRENT_NDET determinants run on up to
+// ROUTE_WORKERS worker contexts at once, one host thread and one stream each: a
+// solve of that size leaves most of the GPU idle while its host loop waits for
+// the Davidson scalars of each iteration, and the other solves fill the gaps.
+// Larger active spaces keep the GPU busy alone and run one at a time on the
+// caller's context.
+constexpr int ROUTE_WORKERS = 4;
+constexpr int64_t ROUTE_CONCURRENT_NDET = 4000000;
+
+// Makes sure the context has k worker contexts.
+static int route_workers(mbe_ctx *ctx, int k)
+{
+    while ((int)ctx->workers.size() < k) {
+        cudaStream_t s = nullptr;
+        MBE_CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        mbe_ctx *w = nullptr;
+        const int rc = mbe_ctx_create(&w, ctx->device, s);
+        if (rc) {
+            cudaStreamDestroy(s);
+            return rc;
+        }
+        ctx->workers.push_back(w);
+        ctx->worker_streams.push_back(s);
+    }
+    return MBE_OK;
 }
 
 // Stream-ordered device buffers released when the call returns, on every path.
@@ -99,7 +129,7 @@ extern "C" int casci_batch_routed(mbe_ctx *ctx, int norb, const double *h1, cons
 
     // Classify: batched (B), one whole-GPU solve each (L), or a one-determinant
     // or malformed active space written directly (D).
-    std::vector<int64_t> rows_b, rows_l, rows_d;
+    std::vector<int64_t> rows_b, rows_l, rows_d, ndet_l;
     std::vector<int32_t> tup_b;
     std::vector<uint8_t> in_ref(norb, 0);
     for (int i = 0; i < n_ref; ++i) in_ref[ref_orbs[i]] = 1;
@@ -121,6 +151,7 @@ extern "C" int casci_batch_routed(mbe_ctx *ctx, int norb, const double *h1, cons
             rows_d.push_back(t);
         } else {
             rows_l.push_back(t);
+            ndet_l.push_back(ndet);
         }
     }
 
@@ -181,17 +212,78 @@ extern "C" int casci_batch_routed(mbe_ctx *ctx, int norb, const double *h1, cons
         const int64_t nl = (int64_t)rows_l.size();
         std::vector<double> eps_l(nl);
         std::vector<int32_t> st_l(nl), it_l(nl);
-        std::vector<int32_t> A(n_cas);
-        for (int64_t i = 0; i < nl; ++i) {
+        auto solve = [&](mbe_ctx *c, int64_t i) -> int {
+            std::vector<int32_t> A(n_cas);
             const int32_t *tp = tup_h.data() + (size_t)rows_l[i] * order;
             std::merge(ref_orbs, ref_orbs + n_ref, tp, tp + order, A.begin());
             double result[3] = {0.0, 0.0, 0.0};
             int32_t info[3] = {0, 0, 0};
-            int rc = casci_solve(ctx, norb, h1, eri, occ, n_cas, A.data(), opts, result, info, nullptr);
+            const int rc = casci_solve(c, norb, h1, eri, occ, n_cas, A.data(), opts, result, info, nullptr);
             if (rc) return rc;
             eps_l[i] = result[1] - e_ref_corr;
             st_l[i] = info[0];
             it_l[i] = (std::min(info[1], 65535) << 16) | std::min(info[2], 65535);
+            return MBE_OK;
+        };
+        std::vector<int64_t> conc, alone;
+        for (int64_t i = 0; i < nl; ++i) (ndet_l[i] <= ROUTE_CONCURRENT_NDET ? conc : alone).push_back(i);
+        const int nw = (int)std::min<int64_t>(ROUTE_WORKERS, (int64_t)conc.size());
+        if (nw >= 2) {
+            int rc = route_workers(ctx, nw);
+            if (rc) return rc;
+            // the workers' streams start after the work queued so far on the caller's
+            cudaEvent_t ready = nullptr;
+            MBE_CU(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+            cudaError_t e = cudaEventRecord(ready, ctx->stream);
+            for (int w = 0; w < nw && e == cudaSuccess; ++w) e = cudaStreamWaitEvent(ctx->worker_streams[w], ready, 0);
+            cudaEventDestroy(ready);
+            MBE_CU(e);
+            std::vector<int64_t> launches0(nw);
+            for (int w = 0; w < nw; ++w) launches0[w] = ctx->workers[w]->launches;
+            std::atomic<int64_t> next{0};
+            std::vector<int> rcs(nw, MBE_OK);
+            std::vector<std::string> msgs(nw);
+            auto work = [&](int w) {
+                if (cudaSetDevice(ctx->device) != cudaSuccess) {
+                    rcs[w] = MBE_ECUDA;
+                    msgs[w] = "casci_batch_routed: cudaSetDevice failed in a worker thread";
+                    next.store((int64_t)conc.size());
+                    return;
+                }
+                for (;;) {
+                    const int64_t j = next.fetch_add(1);
+                    if (j >= (int64_t)conc.size()) break;
+                    const int r = solve(ctx->workers[w], conc[j]);
+                    if (r) {
+                        rcs[w] = r;
+                        msgs[w] = mbe_last_error();
+                        next.store((int64_t)conc.size());
+                        break;
+                    }
+                }
+            };
+            std::vector<std::thread> threads;
+            for (int w = 1; w < nw; ++w) {
+                try {
+                    threads.emplace_back(work, w);
+                } catch (...) {
+                    break;  // fewer threads: the ones running take the rest of the list
+                }
+            }
+            work(0);  // the calling thread drives worker 0
+            for (auto &t : threads) t.join();
+            for (int w = 0; w < nw; ++w) ctx->launches += ctx->workers[w]->launches - launches0[w];
+            for (int w = 0; w < nw; ++w)
+                if (rcs[w]) {
+                    set_error("%s", msgs[w].c_str());
+                    return rcs[w];
+                }
+        } else {
+            alone.insert(alone.end(), conc.begin(), conc.end());
+        }
+        for (const int64_t i : alone) {
+            const int rc = solve(ctx, i);
+            if (rc) return rc;
         }
         void *d_rows = nullptr, *d_eps = nullptr, *d_st = nullptr, *d_it = nullptr;
         MBE_CU(buf.get((size_t)nl * sizeof(int64_t), &d_rows));
