@@ -45,3 +45,14 @@ def test_solver_class_choice(warp_max):
                 assert all(d * 32 < ndet for d in smaller)
             else:
                 assert (solver, dpl) == (1, 0)
+
+
+def test_recorded_traffic_is_gated_by_the_kernel_source(monkeypatch):
+    # the committed DRAM counters count only while the solver sources are the ones
+    # they were taken on; any other source hash reports no traffic
+    key = "k_casci_warp_mixed<13>:order6"
+    got = bench.recorded_traffic(key)
+    assert got is None or (isinstance(got, int) and got > 0)
+    monkeypatch.setattr(bench, "source_hash", lambda: "0000000000000000")
+    assert bench.recorded_traffic(key) is None
+    assert bench.recorded_traffic("no such kernel") is None
